@@ -1,0 +1,174 @@
+/*
+ * pod2g.h — C ABI of a GB300 (sm_103a) solver for parametrized sparse SPD systems
+ *           K(theta) u = f(theta) by POD-2G-preconditioned conjugate gradients.
+ *
+ * Method: arXiv 2207.02543 (Nikolopoulos et al.), Algorithm 3 (PCG whose
+ * preconditioner is one cycle of an algebraic two-grid scheme) with the cycle of
+ * Algorithm 2 and the POD basis Phi_r as prolongation operator (Section 3.3).
+ * The preconditioner applied to a residual r is s = AMG(0; K, r, r1, r2):
+ *     y  <- 0;  r1 damped-Jacobi sweeps  y <- y + omega D^{-1} (r - K y)
+ *     e_c = (Phi^T K Phi)^{-1} Phi^T (r - K y);   y <- y + Phi e_c
+ *     r2 damped-Jacobi sweeps;                    s = y
+ * with D = diag(K). The outer iteration is Algorithm 1 with T^{-1} r := s.
+ *
+ * Conventions
+ *   - n_brows block rows of size bs (1, 2 or 3); n = n_brows * bs unknowns.
+ *   - Pattern: block CSR, int32 row_ptr[n_brows+1], col_idx[nnzb]; columns sorted
+ *     ascending within a row, every diagonal block present, pattern symmetric.
+ *     One pattern is shared by every parameter instance ("slot") of a context.
+ *   - Values of one instance: double values[nnzb * bs * bs], block after block,
+ *     each block row-major.
+ *   - Phi: double phi[n * k], column-major (column j = POD mode j), any
+ *     full-column-rank basis (orthonormality is not required).
+ *   - Vectors (b, x0, x) are double[n] per instance.
+ *   - Stopping rule: ||r_k||_2 <= tol * ||b||_2 on the recurrence residual,
+ *     tested before every iteration (k = 0 included). iters = number of alpha
+ *     updates. final relative residual = ||b - K x||_2 / ||b||_2 recomputed at
+ *     exit. b = 0 gives x = 0, iters = 0, relres = 0.
+ *   - Precision modes:
+ *       POD2G_FP64          values, vectors, Phi and arithmetic in FP64; one
+ *                           instance at a time, kernel by kernel, convergence
+ *                           checked on the host every iteration (the plain path);
+ *       POD2G_MIXED_FP32PHI batched path: values stored in FP32 (the system solved
+ *                           is the one with FP32-rounded values), preconditioner
+ *                           (smoothing, restriction, prolongation, K_c build) in
+ *                           FP32 with FP32 Phi, outer recurrences (x, r, p, K p,
+ *                           dot products) in double-float (~48-bit significand,
+ *                           pairs of FP32, error-free transformations), scalars
+ *                           and the k x k Cholesky factor in FP64;
+ *       POD2G_MIXED_BF16PHI as above with Phi rounded to BF16.
+ *   - Ownership: the library copies every input; callers keep their buffers.
+ *     Output buffers belong to the caller. Functions whose name ends in _dev take
+ *     device pointers, read and written in the context's stream.
+ *   - Thread safety: a context is used by one host thread at a time, except that
+ *     pod2g_submit / pod2g_poll may be called from any thread while the serving
+ *     worker runs (they take the context's queue lock).
+ *   - All functions return a status code (POD2G_OK = 0) unless noted.
+ */
+#ifndef POD2G_H
+#define POD2G_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define POD2G_OK             0  /* success / converged */
+#define POD2G_NOT_CONVERGED  1  /* maxit reached; x holds the last iterate */
+#define POD2G_BREAKDOWN      2  /* p^T K p <= 0 or r^T s <= 0: matrix or preconditioner not SPD */
+#define POD2G_NOT_SPD        3  /* coarse matrix Phi^T K Phi not SPD, or a non-positive diagonal */
+#define POD2G_INVALID_ARG    4  /* bad argument (null pointer, size, slot index, pattern) */
+#define POD2G_ADMISSION      5  /* request refused: over the context's HBM budget / no free slot */
+#define POD2G_OOM            6  /* device allocation failed */
+#define POD2G_CUDA_ERROR     7  /* a CUDA call failed */
+#define POD2G_TIMEOUT        8  /* a bounded device or host wait expired */
+#define POD2G_NONFINITE      9  /* NaN or Inf in an input or an iterate */
+#define POD2G_PENDING       10  /* pod2g_poll: request not finished yet */
+
+/* precision modes */
+#define POD2G_FP64           0
+#define POD2G_MIXED_FP32PHI  1
+#define POD2G_MIXED_BF16PHI  2
+
+typedef struct pod2g_ctx* pod2g_t;
+
+/* Shared sparsity pattern (host arrays, copied by pod2g_create). */
+typedef struct {
+    int32_t n_brows;          /* number of block rows (= block columns) */
+    int32_t bs;               /* block size: 1, 2 or 3 */
+    const int32_t* row_ptr;   /* [n_brows + 1], row_ptr[0] = 0 */
+    const int32_t* col_idx;   /* [row_ptr[n_brows]] */
+} pod2g_pattern;
+
+/* Per-context options; fill with pod2g_default_opts and override. */
+typedef struct {
+    double omega;             /* damped-Jacobi weight (default 2/3); needs omega * rho(D^-1 K) < 2 */
+    int pre;                  /* r1: pre-relaxation sweeps (default 1) */
+    int post;                 /* r2: post-relaxation sweeps (default 1) */
+    int precision;            /* POD2G_FP64 / POD2G_MIXED_FP32PHI / POD2G_MIXED_BF16PHI */
+    int beta_pr;              /* 0: beta = r_{k+1}^T s_{k+1} / r_k^T s_k (Algorithm 1); 1: Polak-Ribiere */
+    int max_batch;            /* number of instance slots (1..256) */
+    size_t hbm_budget;        /* bytes the context may allocate; 0 = no limit */
+    int64_t spin_limit;       /* bound on host polling iterations of a solve (0 = default) */
+    int chunk;                /* PCG iterations per CUDA-graph launch in the batched path (even, default 8) */
+    void* stream;             /* cudaStream_t to run on; NULL = a stream owned by the context */
+} pod2g_opts;
+
+/* Fill *opts with defaults. Never fails. */
+void pod2g_default_opts(pod2g_opts* opts);
+
+/* Create a context for one pattern and one POD basis (Section 3.3: Phi_r is the
+ * prolongation, Phi_r^T the restriction). k may be 0 (no coarse correction: the
+ * preconditioner reduces to r1 + r2 damped-Jacobi sweeps). Allocates all device
+ * memory for max_batch slots. Returns POD2G_ADMISSION if that exceeds hbm_budget. */
+int pod2g_create(const pod2g_pattern* pattern, const double* phi, int k,
+                 const pod2g_opts* opts, pod2g_t* out);
+
+/* Load the matrix values of one parameter instance into a slot and run the
+ * per-instance set-up: D^{-1}, K_c = Phi^T K Phi (eq. POD_ROM) symmetrised, and
+ * its FP64 Cholesky factor. values: nnzb*bs*bs doubles, host memory if
+ * on_device == 0, device memory otherwise. Returns POD2G_NOT_SPD for a
+ * non-positive diagonal entry or an indefinite K_c (the slot is then unusable
+ * until values are set again). */
+int pod2g_set_values(pod2g_t ctx, int slot, const double* values, int on_device);
+
+/* Same for several slots at once: values_dev points to nslots consecutive
+ * instances (nslots * nnzb*bs*bs doubles, device memory). status[i] (host) gets
+ * each slot's set-up status; the return value is the first non-OK status. */
+int pod2g_set_values_batch_dev(pod2g_t ctx, int nslots, const int* slots,
+                               const double* values_dev, int* status);
+
+/* Solve one instance (Algorithm 3). b, x0 (NULL: zero) and x are host arrays of
+ * n doubles. iters / relres may be NULL. */
+int pod2g_solve(pod2g_t ctx, int slot, const double* b, const double* x0, double tol,
+                int maxit, double* x, int* iters, double* relres);
+
+/* Solve nslots instances together (host arrays: b[i], x0[i] (x0 or x0[i] may be
+ * NULL), x[i], each n doubles). iters/relres/status: host arrays of nslots (may
+ * be NULL). Returns the first non-OK per-slot status, or OK. */
+int pod2g_solve_batch(pod2g_t ctx, int nslots, const int* slots, const double* const* b,
+                      const double* const* x0, double tol, int maxit, double* const* x,
+                      int* iters, double* relres, int* status);
+
+/* Device-memory variant: b_dev, x0_dev (NULL: zero) and x_dev hold nslots
+ * consecutive vectors of n doubles. iters/relres/status are host arrays. */
+int pod2g_solve_batch_dev(pod2g_t ctx, int nslots, const int* slots, const double* b_dev,
+                          const double* x0_dev, double tol, int maxit, double* x_dev,
+                          int* iters, double* relres, int* status);
+
+/* Serving. A request carries one instance's values (host, nnzb*bs*bs doubles),
+ * its right-hand side and an optional x0 (host, n doubles each); the library
+ * copies them. Requests are admitted into free slots of the context's batch as
+ * slots free up (continuous batching: converged instances retire and waiting
+ * requests join the running batch between CUDA-graph launches). Returns
+ * POD2G_ADMISSION if the waiting queue already holds max_queue requests
+ * (pod2g_serve_start). *ticket identifies the request. */
+int pod2g_serve_start(pod2g_t ctx, int max_queue);
+int pod2g_submit(pod2g_t ctx, const double* values, const double* b, const double* x0,
+                 double tol, int maxit, uint64_t* ticket);
+/* Non-blocking: POD2G_PENDING until the request finishes; then copies x (host, n
+ * doubles; may be NULL), iters, relres, status (may be NULL), returns OK and
+ * forgets the ticket. latency_s (may be NULL) = submit-to-completion seconds. */
+int pod2g_poll(pod2g_t ctx, uint64_t ticket, double* x, int* iters, double* relres,
+               int* status, double* latency_s);
+int pod2g_serve_stop(pod2g_t ctx);
+
+/* Query sizes: n, nnzb, k, max_batch (any pointer may be NULL). */
+int pod2g_info(pod2g_t ctx, int* n, int* nnzb, int* k, int* max_batch);
+
+/* Number of kernel launches the context has issued (for launch accounting). */
+int64_t pod2g_launch_count(pod2g_t ctx);
+
+/* Free all device memory of the context. NULL is ignored. */
+void pod2g_destroy(pod2g_t ctx);
+
+/* Static message for a status code. Never NULL. */
+const char* pod2g_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POD2G_H */

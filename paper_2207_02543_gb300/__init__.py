@@ -1,0 +1,237 @@
+"""GB300-native POD-2G-preconditioned conjugate gradients (arXiv 2207.02543, Algorithm 3).
+
+Thin Python binding of the C ABI declared in include/pod2g.h: argument marshalling
+only. Every step of the solve runs in the CUDA library libpod2g.so built in this
+directory (see build.py); there is no CPU fallback, and importing the binding
+without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpod2g.so")
+
+OK, NOT_CONVERGED, BREAKDOWN, NOT_SPD, INVALID_ARG, ADMISSION, OOM, CUDA_ERROR, TIMEOUT, NONFINITE, PENDING = range(11)
+FP64, MIXED_FP32PHI, MIXED_BF16PHI = 0, 1, 2
+
+EXPORTS = [
+    "pod2g_default_opts", "pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
+    "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
+    "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_destroy", "pod2g_strerror",
+]
+
+
+class Pattern(C.Structure):
+    _fields_ = [("n_brows", C.c_int32), ("bs", C.c_int32), ("row_ptr", C.POINTER(C.c_int32)),
+                ("col_idx", C.POINTER(C.c_int32))]
+
+
+class Opts(C.Structure):
+    _fields_ = [("omega", C.c_double), ("pre", C.c_int), ("post", C.c_int), ("precision", C.c_int),
+                ("beta_pr", C.c_int), ("max_batch", C.c_int), ("hbm_budget", C.c_size_t),
+                ("spin_limit", C.c_int64), ("chunk", C.c_int), ("stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpod2g.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with `python -m paper_2207_02543_gb300.build` "
+                      "(the solver has no CPU fallback)")
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    IP, DP = C.POINTER(C.c_int), C.POINTER(C.c_double)
+    lib.pod2g_default_opts.argtypes = [C.POINTER(Opts)]
+    lib.pod2g_default_opts.restype = None
+    lib.pod2g_create.argtypes = [C.POINTER(Pattern), DP, I, C.POINTER(Opts), C.POINTER(P)]
+    lib.pod2g_set_values.argtypes = [P, I, P, I]
+    lib.pod2g_set_values_batch_dev.argtypes = [P, I, IP, P, IP]
+    lib.pod2g_solve.argtypes = [P, I, DP, DP, D, I, DP, IP, DP]
+    lib.pod2g_solve_batch.argtypes = [P, I, IP, C.POINTER(DP), C.POINTER(DP), D, I, C.POINTER(DP), IP, DP, IP]
+    lib.pod2g_solve_batch_dev.argtypes = [P, I, IP, P, P, D, I, P, IP, DP, IP]
+    lib.pod2g_serve_start.argtypes = [P, I]
+    lib.pod2g_submit.argtypes = [P, DP, DP, DP, D, I, C.POINTER(C.c_uint64)]
+    lib.pod2g_poll.argtypes = [P, C.c_uint64, DP, IP, DP, IP, DP]
+    lib.pod2g_serve_stop.argtypes = [P]
+    lib.pod2g_info.argtypes = [P, IP, IP, IP, IP]
+    lib.pod2g_launch_count.argtypes = [P]
+    lib.pod2g_launch_count.restype = C.c_int64
+    lib.pod2g_destroy.argtypes = [P]
+    lib.pod2g_destroy.restype = None
+    lib.pod2g_strerror.argtypes = [I]
+    lib.pod2g_strerror.restype = C.c_char_p
+    for name in ("pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
+                 "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
+                 "pod2g_serve_stop", "pod2g_info"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load_library().pod2g_strerror(int(status)).decode()
+
+
+class Pod2gError(RuntimeError):
+    def __init__(self, status, where=""):
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+        self.status = status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _is_cuda(t) -> bool:
+    return hasattr(t, "is_cuda") and t.is_cuda
+
+
+class Solver:
+    """One context: a shared block-CSR pattern, a POD basis Phi (n x k) and `max_batch` instance slots."""
+
+    def __init__(self, row_ptr, col_idx, bs, phi, *, precision=MIXED_FP32PHI, omega=2.0 / 3.0, pre=1, post=1,
+                 beta_pr=False, max_batch=1, hbm_budget=0, chunk=8, spin_limit=0, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        self.col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        phi = np.asarray(phi, dtype=np.float64)
+        if phi.ndim == 1:
+            phi = phi[:, None]
+        self.n = (len(self.row_ptr) - 1) * bs
+        k = phi.shape[1] if phi.size else 0
+        phi_cm = np.asfortranarray(phi) if k else np.zeros(1)
+        pat = Pattern(len(self.row_ptr) - 1, bs, self.row_ptr.ctypes.data_as(C.POINTER(C.c_int32)),
+                      self.col_idx.ctypes.data_as(C.POINTER(C.c_int32)))
+        o = Opts()
+        lib.pod2g_default_opts(C.byref(o))
+        o.omega, o.pre, o.post, o.precision = omega, pre, post, precision
+        o.beta_pr, o.max_batch, o.hbm_budget, o.chunk = int(beta_pr), max_batch, hbm_budget, chunk
+        o.spin_limit = spin_limit
+        o.stream = C.c_void_p(stream) if stream else None
+        h = C.c_void_p()
+        st = lib.pod2g_create(C.byref(pat), phi_cm.ctypes.data_as(C.POINTER(C.c_double)), k, C.byref(o), C.byref(h))
+        if st != OK:
+            raise Pod2gError(st, "pod2g_create")
+        self.h = h
+        self.k, self.bs, self.max_batch, self.precision = k, bs, max_batch, precision
+        self.nnzb = int(self.row_ptr[-1])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.pod2g_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        return int(self._lib.pod2g_launch_count(self.h))
+
+    # -------------------------------------------------------------- set-up
+    def set_values(self, slot: int, values) -> int:
+        """values: numpy float64 (host) or a CUDA float64 tensor, nnzb*bs*bs entries."""
+        if _is_cuda(values):
+            st = self._lib.pod2g_set_values(self.h, slot, C.c_void_p(values.data_ptr()), 1)
+        else:
+            v = _f64(values).reshape(-1)
+            st = self._lib.pod2g_set_values(self.h, slot, v.ctypes.data_as(C.c_void_p), 0)
+        return st
+
+    def set_values_batch_dev(self, slots, values_dev):
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        status = np.zeros(len(slots), dtype=np.int32)
+        st = self._lib.pod2g_set_values_batch_dev(self.h, len(slots), slots.ctypes.data_as(C.POINTER(C.c_int)),
+                                                  C.c_void_p(values_dev.data_ptr()),
+                                                  status.ctypes.data_as(C.POINTER(C.c_int)))
+        return st, status
+
+    # -------------------------------------------------------------- solves
+    def solve(self, slot, b, x0=None, tol=1e-8, maxit=1000):
+        """Single instance, host arrays. Returns (x, iters, relres, status)."""
+        b = _f64(b)
+        x = np.empty(self.n)
+        x0a = _f64(x0) if x0 is not None else None
+        it = C.c_int(0)
+        rr = C.c_double(0)
+        st = self._lib.pod2g_solve(self.h, slot, _dptr(b), _dptr(x0a) if x0a is not None else None, tol, maxit,
+                                   _dptr(x), C.byref(it), C.byref(rr))
+        return x, it.value, rr.value, st
+
+    def solve_batch(self, slots, B, X0=None, tol=1e-8, maxit=1000):
+        """Host arrays B[i], X0[i]. Returns (X, iters, relres, status, rc)."""
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        m = len(slots)
+        Bs = [_f64(B[i]) for i in range(m)]
+        Xs = [np.empty(self.n) for _ in range(m)]
+        X0s = [(_f64(X0[i]) if X0 is not None and X0[i] is not None else None) for i in range(m)]
+        DP = C.POINTER(C.c_double)
+        barr = (DP * m)(*[_dptr(a) for a in Bs])
+        xarr = (DP * m)(*[_dptr(a) for a in Xs])
+        x0arr = (DP * m)(*[(_dptr(a) if a is not None else DP()) for a in X0s]) if X0 is not None else None
+        iters = np.zeros(m, dtype=np.int32)
+        rel = np.zeros(m)
+        status = np.zeros(m, dtype=np.int32)
+        rc = self._lib.pod2g_solve_batch(self.h, m, slots.ctypes.data_as(C.POINTER(C.c_int)), barr, x0arr, tol, maxit,
+                                         xarr, iters.ctypes.data_as(C.POINTER(C.c_int)), _dptr(rel),
+                                         status.ctypes.data_as(C.POINTER(C.c_int)))
+        return np.stack(Xs), iters, rel, status, rc
+
+    def solve_batch_dev(self, slots, b_dev, x_dev, x0_dev=None, tol=1e-8, maxit=1000):
+        """Device tensors b_dev, x_dev (and x0_dev): [len(slots), n] float64 on the context's GPU."""
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        m = len(slots)
+        iters = np.zeros(m, dtype=np.int32)
+        rel = np.zeros(m)
+        status = np.zeros(m, dtype=np.int32)
+        rc = self._lib.pod2g_solve_batch_dev(self.h, m, slots.ctypes.data_as(C.POINTER(C.c_int)),
+                                             C.c_void_p(b_dev.data_ptr()),
+                                             C.c_void_p(x0_dev.data_ptr()) if x0_dev is not None else None, tol, maxit,
+                                             C.c_void_p(x_dev.data_ptr()), iters.ctypes.data_as(C.POINTER(C.c_int)),
+                                             _dptr(rel), status.ctypes.data_as(C.POINTER(C.c_int)))
+        return iters, rel, status, rc
+
+    # -------------------------------------------------------------- serving
+    def serve_start(self, max_queue=1024):
+        st = self._lib.pod2g_serve_start(self.h, max_queue)
+        if st != OK:
+            raise Pod2gError(st, "pod2g_serve_start")
+
+    def submit(self, values, b, x0=None, tol=1e-8, maxit=1000):
+        v = _f64(values).reshape(-1)
+        b = _f64(b)
+        x0a = _f64(x0) if x0 is not None else None
+        t = C.c_uint64(0)
+        st = self._lib.pod2g_submit(self.h, _dptr(v), _dptr(b), _dptr(x0a) if x0a is not None else None, tol, maxit,
+                                    C.byref(t))
+        return st, t.value
+
+    def poll(self, ticket):
+        x = np.empty(self.n)
+        it = C.c_int(0)
+        rr = C.c_double(0)
+        s = C.c_int(0)
+        lat = C.c_double(0)
+        st = self._lib.pod2g_poll(self.h, ticket, _dptr(x), C.byref(it), C.byref(rr), C.byref(s), C.byref(lat))
+        if st != OK:
+            return st, None
+        return OK, dict(x=x, iters=it.value, relres=rr.value, status=s.value, latency_s=lat.value)
+
+    def serve_stop(self):
+        return self._lib.pod2g_serve_stop(self.h)

@@ -1,0 +1,406 @@
+// C ABI of the POD-2G-PCG library (declared in include/pod2g.h): context
+// creation and device memory, per-instance set-up, solves, and the serving worker
+// that admits requests into free slots of the running batch (continuous batching).
+#include "common.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+void pod2g_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+int pod2g_check_launch(pod2g_ctx* c) {
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_last_cuda = e;
+        return POD2G_CUDA_ERROR;
+    }
+    return POD2G_OK;
+}
+
+int dev_alloc(pod2g_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return POD2G_OK;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c->hbm_budget && c->allocated + bytes > c->hbm_budget) return POD2G_ADMISSION;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return POD2G_OOM;
+    }
+    c->allocated += bytes;
+    return POD2G_OK;
+}
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// FP64 -> nearest BF16 (round to nearest even on the FP64 significand), as FP32.
+static float round_bf16(double v) {
+    uint64_t u;
+    std::memcpy(&u, &v, 8);
+    if (((u >> 52) & 0x7ff) == 0x7ff) return (float)v;
+    uint64_t r = u + 0x00001FFFFFFFFFFFull + ((u >> 45) & 1ull);
+    r &= ~0x00001FFFFFFFFFFFull;
+    double d;
+    std::memcpy(&d, &r, 8);
+    return (float)d;
+}
+
+static int pick_kp(int k) {
+    const int list[] = {0, 8, 16, 24, 32, 40, 48, 64};
+    for (int v : list)
+        if (v >= k) return v;
+    return -1;
+}
+
+extern "C" {
+
+void pod2g_default_opts(pod2g_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->omega = 2.0 / 3.0;
+    o->pre = 1;
+    o->post = 1;
+    o->precision = POD2G_MIXED_FP32PHI;
+    o->beta_pr = 0;
+    o->max_batch = 1;
+    o->hbm_budget = 0;
+    o->spin_limit = 0;
+    o->chunk = 8;
+    o->stream = nullptr;
+}
+
+const char* pod2g_strerror(int s) {
+    switch (s) {
+        case POD2G_OK: return "ok";
+        case POD2G_NOT_CONVERGED: return "not converged (maxit reached)";
+        case POD2G_BREAKDOWN: return "breakdown (p^T K p <= 0 or r^T s <= 0)";
+        case POD2G_NOT_SPD: return "not SPD (coarse matrix or diagonal)";
+        case POD2G_INVALID_ARG: return "invalid argument";
+        case POD2G_ADMISSION: return "admission refused (HBM budget or queue full)";
+        case POD2G_OOM: return "device out of memory";
+        case POD2G_CUDA_ERROR: return g_last_cuda != cudaSuccess ? cudaGetErrorString(g_last_cuda) : "CUDA error";
+        case POD2G_TIMEOUT: return "timeout";
+        case POD2G_NONFINITE: return "non-finite value";
+        case POD2G_PENDING: return "pending";
+        default: return "unknown status";
+    }
+}
+
+static void free_all(pod2g_ctx* c) {
+    void* ptrs[] = {c->d_row_ptr, c->d_col_idx, c->d_diag_blk, c->d_phi64, c->d_phi32, c->d_phi16, c->d_Lc,
+                    c->d_setup_status, c->d_stage, c->d_stage32, c->d_W, c->d_ac_part, c->d_Ac, c->d_counters,
+                    c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
+                    c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
+                    c->d_pdf, c->d_qdf, c->d_bdf, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
+                    c->d_mask, c->d_iob, c->d_iox};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_scal64) cudaFreeHost(c->h_scal64);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+void pod2g_destroy(pod2g_ctx* c) {
+    if (!c) return;
+    pod2g_serve_stop(c);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+#define ALLOC(ptr, bytes)                                                      \
+    do {                                                                       \
+        int s_ = dev_alloc(c, (void**)&(ptr), (bytes));                        \
+        if (s_ != POD2G_OK) { free_all(c); delete c; return s_; }              \
+    } while (0)
+
+int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g_opts* opts_in, pod2g_t* out) {
+    if (!out) return POD2G_INVALID_ARG;
+    *out = nullptr;
+    pod2g_opts o;
+    if (opts_in) o = *opts_in; else pod2g_default_opts(&o);
+    if (!pat || !pat->row_ptr || !pat->col_idx || pat->n_brows <= 0 || pat->bs < 1 || pat->bs > 3)
+        return POD2G_INVALID_ARG;
+    if (k < 0 || k > POD2G_MAX_K || (k > 0 && !phi)) return POD2G_INVALID_ARG;
+    if (o.precision < 0 || o.precision > 2 || o.max_batch < 1 || o.max_batch > POD2G_MAX_BP) return POD2G_INVALID_ARG;
+    if (!(o.omega > 0.0) || o.pre < 0 || o.post < 0 || o.pre > 8 || o.post > 8) return POD2G_INVALID_ARG;
+    if (o.precision != POD2G_FP64 && (o.pre > 1 || o.post > 1)) return POD2G_INVALID_ARG;
+    if (o.chunk <= 0) o.chunk = 8;
+    // pattern checks: monotone row_ptr, columns in range and sorted, diagonal present
+    const int nb = pat->n_brows;
+    if (pat->row_ptr[0] != 0) return POD2G_INVALID_ARG;
+    std::vector<int32_t> diag(nb, -1);
+    for (int i = 0; i < nb; ++i) {
+        int a = pat->row_ptr[i], b = pat->row_ptr[i + 1];
+        if (b < a) return POD2G_INVALID_ARG;
+        for (int t = a; t < b; ++t) {
+            int j = pat->col_idx[t];
+            if (j < 0 || j >= nb) return POD2G_INVALID_ARG;
+            if (t > a && j <= pat->col_idx[t - 1]) return POD2G_INVALID_ARG;
+            if (j == i) diag[i] = t;
+        }
+        if (diag[i] < 0) return POD2G_INVALID_ARG;
+    }
+    const int bs = pat->bs;
+    const long long n = (long long)nb * bs;
+    const long long nnzb = pat->row_ptr[nb];
+    if (k > 0) {
+        for (long long e = 0; e < n * k; ++e)
+            if (!std::isfinite(phi[e])) return POD2G_NONFINITE;
+    }
+
+    pod2g_ctx* c = new pod2g_ctx();
+    cudaGetDevice(&c->device);
+    c->nb = nb; c->bs = bs; c->n = (int)n; c->nnzb = (int)nnzb; c->k = k; c->kp = pick_kp(k);
+    c->precision = o.precision; c->pre = o.pre; c->post = o.post; c->beta_pr = o.beta_pr ? 1 : 0;
+    c->B = o.max_batch; c->omega = o.omega; c->hbm_budget = o.hbm_budget; c->spin_limit = o.spin_limit;
+    c->chunk = o.chunk;
+    int Bp = 1;
+    while (Bp < o.max_batch) Bp <<= 1;
+    c->Bp = c->precision == POD2G_FP64 ? 1 : Bp;
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return POD2G_CUDA_ERROR; }
+        c->own_stream = true;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->num_sms = sms > 0 ? sms : 152;
+    const int kp = c->kp;
+    const long long tot = nnzb * bs * bs;
+    const int Gmax = 4 * c->num_sms;
+
+    ALLOC(c->d_row_ptr, sizeof(int32_t) * (nb + 1));
+    ALLOC(c->d_col_idx, sizeof(int32_t) * nnzb);
+    ALLOC(c->d_diag_blk, sizeof(int32_t) * nb);
+    ALLOC(c->d_Lc, sizeof(double) * std::max(1, c->B * k * k));
+    ALLOC(c->d_setup_status, sizeof(int) * c->B);
+    ALLOC(c->d_stage, sizeof(double) * tot);
+    ALLOC(c->d_W, sizeof(double) * std::max(1LL, n * kp));
+    ALLOC(c->d_ac_part, sizeof(double) * std::max(1, 2 * c->num_sms * k * k));
+    ALLOC(c->d_Ac, sizeof(double) * std::max(1, k * k));
+    ALLOC(c->d_counters, sizeof(unsigned) * CNT_N);
+    ALLOC(c->d_iob, sizeof(double) * n * c->B);
+    ALLOC(c->d_iox, sizeof(double) * n * c->B);
+    if (c->precision == POD2G_FP64) {
+        ALLOC(c->d_phi64, sizeof(double) * std::max(1LL, n * kp));
+        ALLOC(c->d_vals64, sizeof(double) * tot * c->B);
+        ALLOC(c->d_dinv64, sizeof(double) * n * c->B);
+        double** vecs[] = {&c->d_x64, &c->d_r64, &c->d_s64, &c->d_p64, &c->d_q64, &c->d_y64, &c->d_t64, &c->d_w64};
+        for (double** v : vecs) ALLOC(*v, sizeof(double) * n);
+        ALLOC(c->d_c64, sizeof(double) * std::max(1, kp));
+        ALLOC(c->d_part64, sizeof(double) * (size_t)Gmax * (kp + 8));
+        ALLOC(c->d_scal64, sizeof(double) * 16);
+        if (cudaMallocHost(&c->h_scal64, sizeof(double) * 16) != cudaSuccess) { free_all(c); delete c; return POD2G_OOM; }
+    } else {
+        ALLOC(c->d_phi32, sizeof(float) * std::max(1LL, n * kp));
+        ALLOC(c->d_stage32, sizeof(float) * tot);
+        ALLOC(c->d_vals32, sizeof(float) * tot * Bp);
+        ALLOC(c->d_dinv32, sizeof(float) * n * Bp);
+        ALLOC(c->d_xdf, sizeof(float2) * n * Bp);
+        ALLOC(c->d_rdf, sizeof(float2) * n * Bp);
+        ALLOC(c->d_pdf, sizeof(float2) * n * Bp);
+        ALLOC(c->d_qdf, sizeof(float2) * n * Bp);
+        ALLOC(c->d_bdf, sizeof(float2) * n * Bp);
+        ALLOC(c->d_s32, sizeof(float) * n * Bp);
+        ALLOC(c->d_y32, sizeof(float) * n * Bp);
+        ALLOC(c->d_ec, sizeof(float) * std::max(1, Bp * kp));
+        ALLOC(c->d_part, sizeof(double) * Gmax * Bp * 2);
+        ALLOC(c->d_cpart, sizeof(double) * (size_t)Gmax * Bp * std::max(1, kp));
+        ALLOC(c->d_sc, sizeof(SlotScalars) * Bp);
+        ALLOC(c->d_mask, sizeof(int) * 2 * Bp);
+        if (cudaMallocHost(&c->h_sc, sizeof(SlotScalars) * Bp) != cudaSuccess) { free_all(c); delete c; return POD2G_OOM; }
+        std::memset(c->h_sc, 0, sizeof(SlotScalars) * Bp);
+        if (batched_alloc(c) != POD2G_OK) { free_all(c); delete c; return POD2G_INVALID_ARG; }
+    }
+    c->setup_ok.assign(c->B, 0);
+    // uploads (synchronous, once)
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = up(c->d_row_ptr, pat->row_ptr, sizeof(int32_t) * (nb + 1)) &&
+              up(c->d_col_idx, pat->col_idx, sizeof(int32_t) * nnzb) &&
+              up(c->d_diag_blk, diag.data(), sizeof(int32_t) * nb) &&
+              cudaMemset(c->d_counters, 0, sizeof(unsigned) * CNT_N) == cudaSuccess;
+    if (ok && kp > 0) {
+        if (c->precision == POD2G_FP64) {
+            std::vector<double> h(n * kp, 0.0);
+            for (long long d = 0; d < n; ++d)
+                for (int m = 0; m < k; ++m) h[d * kp + m] = phi[(long long)m * n + d];
+            ok = up(c->d_phi64, h.data(), sizeof(double) * n * kp);
+        } else {
+            std::vector<float> h(n * kp, 0.f);
+            for (long long d = 0; d < n; ++d)
+                for (int m = 0; m < k; ++m) {
+                    double v = phi[(long long)m * n + d];
+                    h[d * kp + m] = c->precision == POD2G_MIXED_BF16PHI ? round_bf16(v) : (float)v;
+                }
+            ok = up(c->d_phi32, h.data(), sizeof(float) * n * kp);
+        }
+    }
+    if (ok && c->precision != POD2G_FP64) {
+        ok = cudaMemset(c->d_sc, 0, sizeof(SlotScalars) * Bp) == cudaSuccess &&
+             cudaMemset(c->d_vals32, 0, sizeof(float) * tot * Bp) == cudaSuccess &&
+             cudaMemset(c->d_dinv32, 0, sizeof(float) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_xdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_rdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_pdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_qdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_bdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_s32, 0, sizeof(float) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_y32, 0, sizeof(float) * n * Bp) == cudaSuccess;
+    }
+    if (!ok) {
+        g_last_cuda = cudaGetLastError();
+        free_all(c);
+        delete c;
+        return POD2G_CUDA_ERROR;
+    }
+    *out = c;
+    return POD2G_OK;
+}
+
+int pod2g_info(pod2g_t c, int* n, int* nnzb, int* k, int* max_batch) {
+    if (!c) return POD2G_INVALID_ARG;
+    if (n) *n = c->n;
+    if (nnzb) *nnzb = c->nnzb;
+    if (k) *k = c->k;
+    if (max_batch) *max_batch = c->B;
+    return POD2G_OK;
+}
+
+int64_t pod2g_launch_count(pod2g_t c) { return c ? (int64_t)c->launches : 0; }
+
+static int finish_setup(pod2g_ctx* c, int nslots, const int* slots, int* status) {
+    std::vector<int> st(c->B, 0);
+    cudaError_t e = cudaMemcpyAsync(st.data(), c->d_setup_status, sizeof(int) * c->B, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { g_last_cuda = e; return POD2G_CUDA_ERROR; }
+    int first = POD2G_OK;
+    for (int i = 0; i < nslots; ++i) {
+        int s = st[slots[i]];
+        c->setup_ok[slots[i]] = (s == POD2G_OK);
+        if (status) status[i] = s;
+        if (s != POD2G_OK && first == POD2G_OK) first = s;
+    }
+    return first;
+}
+
+int pod2g_set_values(pod2g_t c, int slot, const double* values, int on_device) {
+    if (!c || !values || slot < 0 || slot >= c->B) return POD2G_INVALID_ARG;
+    if (c->serving) return POD2G_INVALID_ARG;
+    const size_t bytes = sizeof(double) * (size_t)c->nnzb * c->bs * c->bs;
+    const double* src = values;
+    if (!on_device) {
+        P2G_CUDA(cudaMemcpyAsync(c->d_stage, values, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = c->d_stage;
+    }
+    c->setup_ok[slot] = 0;
+    P2G_TRY(setup_values(c, slot, src));
+    return finish_setup(c, 1, &slot, nullptr);
+}
+
+int pod2g_set_values_batch_dev(pod2g_t c, int nslots, const int* slots, const double* values_dev, int* status) {
+    if (!c || !slots || !values_dev || nslots < 1 || nslots > c->B) return POD2G_INVALID_ARG;
+    if (c->serving) return POD2G_INVALID_ARG;
+    const size_t tot = (size_t)c->nnzb * c->bs * c->bs;
+    for (int i = 0; i < nslots; ++i) {
+        if (slots[i] < 0 || slots[i] >= c->B) return POD2G_INVALID_ARG;
+        c->setup_ok[slots[i]] = 0;
+        P2G_TRY(setup_values(c, slots[i], values_dev + i * tot));
+    }
+    return finish_setup(c, nslots, slots, status);
+}
+
+static int check_slots(pod2g_ctx* c, int nslots, const int* slots) {
+    if (nslots < 1 || nslots > c->B || !slots) return POD2G_INVALID_ARG;
+    std::vector<char> seen(c->B, 0);
+    for (int i = 0; i < nslots; ++i) {
+        int s = slots[i];
+        if (s < 0 || s >= c->B || seen[s] || !c->setup_ok[s]) return POD2G_INVALID_ARG;
+        seen[s] = 1;
+    }
+    return POD2G_OK;
+}
+
+int pod2g_solve_batch_dev(pod2g_t c, int nslots, const int* slots, const double* b_dev, const double* x0_dev,
+                          double tol, int maxit, double* x_dev, int* iters, double* relres, int* status) {
+    if (!c || !b_dev || !x_dev || !(tol >= 0.0) || maxit < 0) return POD2G_INVALID_ARG;
+    if (c->serving) return POD2G_INVALID_ARG;
+    P2G_TRY(check_slots(c, nslots, slots));
+    std::vector<int> st(nslots, POD2G_OK);
+    if (c->precision == POD2G_FP64) {
+        for (int i = 0; i < nslots; ++i) {
+            int it = 0;
+            double rr = 0.0;
+            P2G_TRY(plain_solve(c, slots[i], b_dev + (size_t)i * c->n, x0_dev ? x0_dev + (size_t)i * c->n : nullptr,
+                                tol, maxit, x_dev + (size_t)i * c->n, &it, &rr, &st[i]));
+            if (iters) iters[i] = it;
+            if (relres) relres[i] = rr;
+        }
+    } else {
+        // lane = slot index: slots >= Bp cannot occur (B <= Bp)
+        std::vector<double> tols(nslots, tol);
+        std::vector<int> maxits(nslots, maxit);
+        P2G_TRY(batched_load(c, nslots, slots, b_dev, x0_dev, tols.data(), maxits.data()));
+        std::vector<int> lanes(slots, slots + nslots);
+        P2G_TRY(batched_run(c, lanes));
+        P2G_TRY(batched_finalize(c, nslots, slots, x_dev, iters, relres, st.data()));
+    }
+    int first = POD2G_OK;
+    for (int i = 0; i < nslots; ++i) {
+        if (status) status[i] = st[i];
+        if (st[i] != POD2G_OK && first == POD2G_OK) first = st[i];
+    }
+    return first;
+}
+
+int pod2g_solve_batch(pod2g_t c, int nslots, const int* slots, const double* const* b, const double* const* x0,
+                      double tol, int maxit, double* const* x, int* iters, double* relres, int* status) {
+    if (!c || !b || !x) return POD2G_INVALID_ARG;
+    P2G_TRY(check_slots(c, nslots, slots));
+    const size_t n = c->n;
+    bool any_x0 = false;
+    for (int i = 0; i < nslots; ++i) {
+        if (!b[i] || !x[i]) return POD2G_INVALID_ARG;
+        if (x0 && x0[i]) any_x0 = true;
+    }
+    for (int i = 0; i < nslots; ++i) {
+        P2G_CUDA(cudaMemcpyAsync(c->d_iob + i * n, b[i], sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        if (any_x0) {
+            if (x0[i]) {
+                P2G_CUDA(cudaMemcpyAsync(c->d_iox + i * n, x0[i], sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+            } else {
+                P2G_CUDA(cudaMemsetAsync(c->d_iox + i * n, 0, sizeof(double) * n, c->stream));
+            }
+        }
+    }
+    // x is written into d_iob's rows after b has been consumed: use a separate region
+    int rc = pod2g_solve_batch_dev(c, nslots, slots, c->d_iob, any_x0 ? c->d_iox : nullptr, tol, maxit, c->d_iox,
+                                   iters, relres, status);
+    if (rc == POD2G_INVALID_ARG || rc == POD2G_CUDA_ERROR || rc == POD2G_TIMEOUT) return rc;
+    for (int i = 0; i < nslots; ++i)
+        P2G_CUDA(cudaMemcpyAsync(x[i], c->d_iox + i * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    P2G_CUDA(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+int pod2g_solve(pod2g_t c, int slot, const double* b, const double* x0, double tol, int maxit, double* x, int* iters,
+                double* relres) {
+    const double* bb[1] = {b};
+    const double* xx0[1] = {x0};
+    double* xx[1] = {x};
+    int st = 0;
+    int rc = pod2g_solve_batch(c, 1, &slot, bb, x0 ? xx0 : nullptr, tol, maxit, xx, iters, relres, &st);
+    return rc;
+}
+
+}  // extern "C"

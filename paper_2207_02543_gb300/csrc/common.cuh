@@ -1,0 +1,250 @@
+// Shared definitions of the POD-2G-PCG library: context layout, error handling,
+// double-float arithmetic and block-reduction helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/pod2g.h"
+
+#define POD2G_THREADS 256      // threads per CTA of the row kernels
+#define POD2G_MAX_K 64         // largest supported number of POD modes
+#define POD2G_MAX_BP 256       // largest slot-lane count
+
+// ---------------------------------------------------------------------------- slot states
+enum SlotState : int { SLOT_IDLE = 0, SLOT_JOINING = 1, SLOT_ACTIVE = 2, SLOT_DONE = 3 };
+
+// Per-slot scalars of the batched PCG (device memory, one entry per slot lane).
+struct SlotScalars {
+    double rs;      // r_k^T s_k
+    double alpha;
+    double beta;
+    double bb;      // ||b||^2
+    double tol2;    // tol^2 ||b||^2
+    double rr;      // ||r_k||^2 (recurrence residual)
+    double relres;  // final true relative residual
+    int state;      // SlotState
+    int result;     // POD2G_* status once DONE
+    int iters;
+    int maxit;
+    int first;      // 1 while the initial preconditioner pass runs (beta forced to 0)
+    int pad;
+};
+
+// ---------------------------------------------------------------------------- context
+struct ServeRequest;
+
+struct pod2g_ctx {
+    int device = 0;
+    int nb = 0, bs = 0, n = 0, nnzb = 0, k = 0, kp = 0;   // kp: k padded to a multiple of 4
+    int precision = 0, pre = 1, post = 1, beta_pr = 0, B = 1, Bp = 1, chunk = 8;
+    double omega = 2.0 / 3.0;
+    size_t hbm_budget = 0, allocated = 0;
+    int64_t spin_limit = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::atomic<int64_t> launches{0};
+    int num_sms = 152;
+
+    // pattern
+    int32_t* d_row_ptr = nullptr;
+    int32_t* d_col_idx = nullptr;
+    int32_t* d_diag_blk = nullptr;      // [nb] index of each block row's diagonal block
+
+    // POD basis, row-major [n][kp] (entries beyond k are zero)
+    double* d_phi64 = nullptr;          // FP64 path
+    float* d_phi32 = nullptr;           // mixed paths (BF16-rounded values for MIXED_BF16PHI)
+    __nv_bfloat16* d_phi16 = nullptr;   // MIXED_BF16PHI: the basis as stored BF16
+
+    // per-slot set-up results
+    double* d_Lc = nullptr;             // [B][k][k] Cholesky factors (FP64)
+    int* d_setup_status = nullptr;      // [B]
+    std::vector<int> setup_ok;          // host copy: slot has a valid set-up
+
+    // set-up scratch (one instance at a time)
+    double* d_stage = nullptr;          // [nnzb*bs*bs] FP64 values staging
+    float* d_stage32 = nullptr;         // [nnzb*bs*bs] FP32-rounded values (mixed paths)
+    double* d_W = nullptr;              // [n][kp]: K Phi (FP64 accumulate)
+    double* d_ac_part = nullptr;        // [G][k][k] contraction partials
+    double* d_Ac = nullptr;             // [k][k]
+    unsigned* d_counters = nullptr;     // last-CTA counters (several)
+
+    // ---- plain FP64 path (slot-major)
+    double* d_vals64 = nullptr;         // [B][nnzb][bs*bs]
+    double* d_dinv64 = nullptr;         // [B][n]
+    double *d_x64 = nullptr, *d_r64 = nullptr, *d_s64 = nullptr, *d_p64 = nullptr, *d_q64 = nullptr,
+           *d_y64 = nullptr, *d_t64 = nullptr, *d_w64 = nullptr;
+    double* d_c64 = nullptr;            // [kp] restriction / coarse vector
+    double* d_part64 = nullptr;         // [G * (kp+4)] reduction partials
+    double* d_scal64 = nullptr;         // [16] plain-path scalars
+    double* h_scal64 = nullptr;         // pinned host mirror
+
+    // ---- batched mixed path (slot-interleaved: element (row, slot) at row*Bp + slot)
+    float* d_vals32 = nullptr;          // [nnzb][bs*bs][Bp]
+    float* d_dinv32 = nullptr;          // [n][Bp]
+    float2* d_xdf = nullptr;            // [n][Bp] double-float
+    float2* d_rdf = nullptr;
+    float2* d_pdf = nullptr;
+    float2* d_qdf = nullptr;
+    float2* d_bdf = nullptr;
+    float* d_s32 = nullptr;             // [n][Bp]
+    float* d_y32 = nullptr;             // [n][Bp]
+    float* d_ec = nullptr;              // [Bp][kp] coarse corrections
+    double* d_part = nullptr;           // reduction partials [G][Bp][2] (scalars)
+    double* d_cpart = nullptr;          // restriction partials [G][Bp][kp]
+    SlotScalars* d_sc = nullptr;        // [Bp]
+    SlotScalars* h_sc = nullptr;        // pinned host mirror
+    int* d_mask = nullptr;              // [2 Bp] lane mask and slot list for load / finalize
+    double* d_iob = nullptr;            // [B][n] staging of right-hand sides (host-buffer entry points)
+    double* d_iox = nullptr;            // [B][n] staging of x0 / x
+    int grid_rows = 0;                  // CTAs of the row kernels
+    int smem_pre = 0;                   // dynamic shared memory of the restriction kernel
+    cudaGraphExec_t graph_exec = nullptr;
+
+    // serving
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread worker;
+    bool serving = false, stop = false;
+    int max_queue = 0;
+    uint64_t next_ticket = 1;
+    std::deque<ServeRequest*> queue;
+    std::map<uint64_t, ServeRequest*> finished;
+    std::map<uint64_t, ServeRequest*> inflight;
+};
+
+struct ServeRequest {
+    uint64_t ticket;
+    std::vector<double> values, b, x0, x;
+    bool has_x0 = false;
+    double tol = 1e-8;
+    int maxit = 1000;
+    int iters = 0, status = POD2G_PENDING;
+    double relres = 0.0;
+    double t_submit = 0.0, t_done = 0.0;
+    int slot = -1;
+};
+
+// ---------------------------------------------------------------------------- errors
+#define P2G_CUDA(call)                                                          \
+    do {                                                                        \
+        cudaError_t e__ = (call);                                               \
+        if (e__ != cudaSuccess) {                                               \
+            pod2g_set_last_cuda_error(e__);                                     \
+            return POD2G_CUDA_ERROR;                                            \
+        }                                                                       \
+    } while (0)
+
+#define P2G_TRY(call)                                                           \
+    do {                                                                        \
+        int s__ = (call);                                                       \
+        if (s__ != POD2G_OK) return s__;                                        \
+    } while (0)
+
+void pod2g_set_last_cuda_error(cudaError_t e);
+int pod2g_check_launch(pod2g_ctx* c);  // counts a launch, checks cudaGetLastError
+
+static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------- double-float
+// Unevaluated sums hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2): a ~48-bit
+// significand carried in FP32 arithmetic. Built from the error-free
+// transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and TwoProd via FMA, and the
+// double-word algorithms of Joldes, Muller and Popescu (ACM TOMS 44(2), 2017).
+// Operations are written so that no multiply-add pair can be contracted.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ float2 df_norm(float hi, float lo) {
+    float s, e;
+    fast_two_sum(hi, lo, s, e);
+    return make_float2(s, e);
+}
+// a + b, both double-float ("AccurateDWPlusDW")
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float sh, sl, th, tl;
+    two_sum(a.x, b.x, sh, sl);
+    two_sum(a.y, b.y, th, tl);
+    sl = __fadd_rn(sl, th);
+    fast_two_sum(sh, sl, sh, sl);
+    sl = __fadd_rn(sl, tl);
+    return df_norm(sh, sl);
+}
+// a * b, both double-float ("DWTimesDW")
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    float ph = __fmul_rn(a.x, b.x);
+    float pl = __fmaf_rn(a.x, b.x, -ph);
+    pl = __fmaf_rn(a.x, b.y, pl);
+    pl = __fmaf_rn(a.y, b.x, pl);
+    return df_norm(ph, pl);
+}
+// accumulator (hi, lo) += v * (ph + pl) for an FP32 v: the product v*ph is
+// split exactly, its high part added with TwoSum, all low parts gathered in lo.
+__device__ __forceinline__ void df_acc_fma(float& hi, float& lo, float v, float ph, float pl) {
+    float p = __fmul_rn(v, ph);
+    float pe = __fmaf_rn(v, ph, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    lo = __fmaf_rn(v, pl, lo);
+}
+__device__ __forceinline__ float2 df_from_double(double d) {
+    float hi = __double2float_rn(d);
+    float lo = __double2float_rn(d - (double)hi);
+    return make_float2(hi, lo);
+}
+__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// ---------------------------------------------------------------------------- last-CTA pattern
+// Every CTA calls this after writing its partial results; it returns true in
+// exactly one CTA (the last to arrive), which may then read all partials. No
+// CTA waits for another, so nothing can hang. The counter is reset by the last CTA.
+__device__ __forceinline__ bool last_cta_arrive(unsigned* counter) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(counter, 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+__device__ __forceinline__ void last_cta_reset(unsigned* counter) {
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// counters used by the last-CTA reductions (indices into ctx->d_counters)
+enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT_W = 5, CNT_N = 16 };
+
+// ---------------------------------------------------------------------------- internal entry points
+int plain_solve(pod2g_ctx* c, int slot, const double* b_dev, const double* x0_dev, double tol, int maxit,
+                double* x_dev, int* iters, double* relres, int* status);
+int setup_values(pod2g_ctx* c, int slot, const double* vals_dev);
+int batched_load(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, const double* x0_dev,
+                 const double* tol, const int* maxit);
+int batched_run(pod2g_ctx* c, const std::vector<int>& lanes);
+int batched_chunk(pod2g_ctx* c);
+int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, int* iters, double* relres,
+                     int* status);
+int batched_alloc(pod2g_ctx* c);
+void batched_free(pod2g_ctx* c);
+int dev_alloc(pod2g_ctx* c, void** p, size_t bytes);

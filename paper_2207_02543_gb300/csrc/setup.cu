@@ -1,0 +1,238 @@
+// Per-instance set-up (one slot): matrix values into the solver's layout, the
+// Jacobi diagonal D^{-1}, the Galerkin coarse matrix K_c = Phi^T K Phi
+// (arXiv 2207.02543, Section 3.3, eq. POD_ROM) symmetrised, and its Cholesky
+// factor in FP64 (the k x k coarse solve of Algorithm 2 with P = Phi_r).
+//
+// Mixed paths: K Phi is formed in double-float from FP32 values and the FP32 (or
+// BF16-rounded) basis, whose products are exact; the contraction Phi^T (K Phi)
+// accumulates double-float per thread and FP64 across threads and CTAs. K Phi
+// of a smooth mode is ~h^2 smaller than |K||Phi|, so FP32 accumulation would lose
+// most digits of K_c; double-float keeps ~14.
+// FP64 path: the same steps in FP64.
+#include "common.cuh"
+
+namespace {
+
+// values (FP64, one instance, [nnzb][bs*bs]) -> FP32 contiguous copy and the
+// slot's lane of the interleaved array [nnzb*bs*bs][Bp]
+__global__ void k_convert_values(const double* __restrict__ v64, float* __restrict__ v32_stage,
+                                 float* __restrict__ vals32, long long total, int Bp, int slot) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        float v = __double2float_rn(v64[e]);
+        v32_stage[e] = v;
+        vals32[e * Bp + slot] = v;
+    }
+}
+
+// D^{-1}: one thread per unknown. status[0] set to NOT_SPD on a non-positive or
+// non-finite diagonal entry.
+template <typename V>
+__global__ void k_dinv(const V* __restrict__ vals, const int32_t* __restrict__ diag_blk, int nb, int bs,
+                       double* __restrict__ dinv64, float* __restrict__ dinv32, int Bp, int slot,
+                       int* __restrict__ status) {
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nb * bs) return;
+    int i = d / bs, rr = d - i * bs;
+    double a = (double)vals[(long long)diag_blk[i] * bs * bs + rr * bs + rr];
+    if (!(a > 0.0) || !isfinite(a)) {
+        atomicExch(status, (int)POD2G_NOT_SPD);
+        a = 1.0;
+    }
+    if (dinv64) dinv64[d] = 1.0 / a;
+    if (dinv32) dinv32[(long long)d * Bp + slot] = (float)(1.0 / a);
+}
+
+// W = K Phi, double-float, one thread per (unknown row, mode m).
+__global__ void k_w_df(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                       const float* __restrict__ v32, const float* __restrict__ phi, int nb, int bs, int kp,
+                       float2* __restrict__ W) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)nb * bs * kp;
+    if (t >= total) return;
+    int m = (int)(t % kp);
+    long long d = t / kp;
+    int i = (int)(d / bs), rr = (int)(d - (long long)i * bs);
+    float hi = 0.f, lo = 0.f;
+    for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
+        int j = col_idx[blk];
+        const float* vb = v32 + (long long)blk * bs * bs + rr * bs;
+        for (int cc = 0; cc < bs; ++cc)
+            df_acc_fma(hi, lo, vb[cc], phi[((long long)j * bs + cc) * kp + m], 0.f);
+    }
+    W[d * kp + m] = df_norm(hi, lo);
+}
+
+// W = K Phi in FP64.
+__global__ void k_w_f64(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                        const double* __restrict__ v64, const double* __restrict__ phi, int nb, int bs, int kp,
+                        double* __restrict__ W) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)nb * bs * kp;
+    if (t >= total) return;
+    int m = (int)(t % kp);
+    long long d = t / kp;
+    int i = (int)(d / bs), rr = (int)(d - (long long)i * bs);
+    double acc = 0.0;
+    for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
+        int j = col_idx[blk];
+        const double* vb = v64 + (long long)blk * bs * bs + rr * bs;
+        for (int cc = 0; cc < bs; ++cc) acc = fma(vb[cc], phi[((long long)j * bs + cc) * kp + m], acc);
+    }
+    W[d * kp + m] = acc;
+}
+
+#define AC_TILE 32
+
+// Contraction K_c = Phi^T W (k x k), split over CTAs along the n rows; the last
+// CTA sums the partials in CTA order (deterministic), symmetrises, and factors
+// K_c = L L^T in FP64. status gets NOT_SPD if a pivot is not positive.
+template <bool DF>
+__global__ void k_ac(const void* __restrict__ phi_v, const void* __restrict__ W_v, long long n, int k, int kp,
+                     double* __restrict__ part, unsigned* counter, double* __restrict__ Ac,
+                     double* __restrict__ Lout, int* __restrict__ status) {
+    // tile of AC_TILE rows of Phi and W in shared memory; FP64 path uses s_d*,
+    // double-float path s_f* (Phi as float, W as (hi, lo) floats)
+    __shared__ double s_dphi[DF ? 1 : AC_TILE][POD2G_MAX_K];
+    __shared__ double s_dw[DF ? 1 : AC_TILE][POD2G_MAX_K];
+    __shared__ float s_fphi[DF ? AC_TILE : 1][POD2G_MAX_K];
+    __shared__ float2 s_fw[DF ? AC_TILE : 1][POD2G_MAX_K];
+    const int npairs = k * k;
+    const int per = (npairs + blockDim.x - 1) / blockDim.x;  // pairs per thread (<= 16)
+    double acc[16];
+    float acc_hi[16], acc_lo[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) { acc[q] = 0.0; acc_hi[q] = 0.f; acc_lo[q] = 0.f; }
+    long long rows_per_cta = (n + gridDim.x - 1) / gridDim.x;
+    long long r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+    for (long long base = r0; base < r1; base += AC_TILE) {
+        int cnt = (int)min((long long)AC_TILE, r1 - base);
+        __syncthreads();
+        for (int e = threadIdx.x; e < AC_TILE * k; e += blockDim.x) {
+            int rr = e / k, m = e - rr * k;
+            long long idx = (base + rr) * kp + m;
+            if (DF) {
+                s_fphi[rr][m] = rr < cnt ? ((const float*)phi_v)[idx] : 0.f;
+                s_fw[rr][m] = rr < cnt ? ((const float2*)W_v)[idx] : make_float2(0.f, 0.f);
+            } else {
+                s_dphi[rr][m] = rr < cnt ? ((const double*)phi_v)[idx] : 0.0;
+                s_dw[rr][m] = rr < cnt ? ((const double*)W_v)[idx] : 0.0;
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < per; ++q) {
+            int pr = threadIdx.x + q * blockDim.x;
+            if (pr >= npairs) break;
+            int m1 = pr / k, m2 = pr - m1 * k;
+            if (DF) {
+                // products Phi (FP32) x W (double-float) accumulated in double-float
+                float hi = acc_hi[q], lo = acc_lo[q];
+                for (int rr = 0; rr < cnt; ++rr) {
+                    float2 w = s_fw[rr][m2];
+                    df_acc_fma(hi, lo, s_fphi[rr][m1], w.x, w.y);
+                }
+                acc_hi[q] = hi;
+                acc_lo[q] = lo;
+            } else {
+                double a = acc[q];
+                for (int rr = 0; rr < cnt; ++rr) a = fma(s_dphi[rr][m1], s_dw[rr][m2], a);
+                acc[q] = a;
+            }
+        }
+    }
+    for (int q = 0; q < per; ++q) {
+        int pr = threadIdx.x + q * blockDim.x;
+        if (pr >= npairs) break;
+        part[(long long)blockIdx.x * npairs + pr] = DF ? ((double)acc_hi[q] + (double)acc_lo[q]) : acc[q];
+    }
+    if (!last_cta_arrive(counter)) return;
+    // ---- last CTA: reduce partials in CTA order
+    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < (int)gridDim.x; ++g) s += part[(long long)g * npairs + pr];
+        Ac[pr] = s;
+    }
+    __syncthreads();
+    // symmetrise into L (lower triangle used)
+    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+        int i = pr / k, j = pr - i * k;
+        Lout[pr] = 0.5 * (Ac[i * k + j] + Ac[j * k + i]);
+    }
+    __syncthreads();
+    // right-looking Cholesky in place (lower triangle), FP64
+    __shared__ int fail;
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            double d = Lout[j * k + j];
+            if (!(d > 0.0) || !isfinite(d)) { fail = 1; d = 1.0; }
+            Lout[j * k + j] = sqrt(d);
+        }
+        __syncthreads();
+        double ljj = Lout[j * k + j];
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) Lout[i * k + j] /= ljj;
+        __syncthreads();
+        int m = k - j - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = j + 1 + e / m, t = j + 1 + e % m;
+            if (t <= i) Lout[i * k + t] -= Lout[i * k + j] * Lout[t * k + j];
+        }
+        __syncthreads();
+    }
+    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+        int i = pr / k, j = pr - i * k;
+        if (j > i) Lout[pr] = 0.0;
+    }
+    if (threadIdx.x == 0 && fail) atomicExch(status, (int)POD2G_NOT_SPD);
+    last_cta_reset(counter);
+}
+
+}  // namespace
+
+int setup_values(pod2g_ctx* c, int slot, const double* vals_dev) {
+    const long long total = (long long)c->nnzb * c->bs * c->bs;
+    const int T = POD2G_THREADS;
+    const int n = c->n;
+    const int32_t* diag_blk = c->d_diag_blk;
+    P2G_CUDA(cudaMemsetAsync(c->d_setup_status + slot, 0, sizeof(int), c->stream));
+    int* st = c->d_setup_status + slot;
+    double* L = c->d_Lc + (size_t)slot * c->k * c->k;
+    if (c->precision == POD2G_FP64) {
+        double* v = c->d_vals64 + (size_t)slot * total;
+        if (v != vals_dev)
+            P2G_CUDA(cudaMemcpyAsync(v, vals_dev, total * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        k_dinv<double><<<ceil_div(n, T), T, 0, c->stream>>>(v, diag_blk, c->nb, c->bs,
+                                                             c->d_dinv64 + (size_t)slot * n, nullptr, 1, 0, st);
+        P2G_TRY(pod2g_check_launch(c));
+        if (c->k > 0) {
+            long long tw = (long long)n * c->kp;
+            k_w_f64<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, v, c->d_phi64, c->nb, c->bs,
+                                                          c->kp, c->d_W);
+            P2G_TRY(pod2g_check_launch(c));
+            int g = std::max(1, std::min(2 * c->num_sms, ceil_div(n, 256)));
+            k_ac<false><<<g, T, 0, c->stream>>>(c->d_phi64, c->d_W, n, c->k, c->kp, c->d_ac_part,
+                                                c->d_counters + CNT_AC, c->d_Ac, L, st);
+            P2G_TRY(pod2g_check_launch(c));
+        }
+    } else {
+        float* stage32 = c->d_stage32;
+        int g = std::min(ceil_div(total, T), 8 * c->num_sms);
+        k_convert_values<<<g, T, 0, c->stream>>>(vals_dev, stage32, c->d_vals32, total, c->Bp, slot);
+        P2G_TRY(pod2g_check_launch(c));
+        k_dinv<float><<<ceil_div(n, T), T, 0, c->stream>>>(stage32, diag_blk, c->nb, c->bs, nullptr, c->d_dinv32,
+                                                            c->Bp, slot, st);
+        P2G_TRY(pod2g_check_launch(c));
+        if (c->k > 0) {
+            long long tw = (long long)n * c->kp;
+            k_w_df<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, stage32, c->d_phi32, c->nb,
+                                                         c->bs, c->kp, (float2*)c->d_W);
+            P2G_TRY(pod2g_check_launch(c));
+            int ga = std::max(1, std::min(2 * c->num_sms, ceil_div(n, 256)));
+            k_ac<true><<<ga, T, 0, c->stream>>>(c->d_phi32, c->d_W, n, c->k, c->kp, c->d_ac_part,
+                                                c->d_counters + CNT_AC, c->d_Ac, L, st);
+            P2G_TRY(pod2g_check_launch(c));
+        }
+    }
+    return POD2G_OK;
+}
