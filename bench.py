@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark: batched mixed-precision POD-2G-PCG on one GB300.
+
+Metric: solves/s at relative residual 1e-8 (arXiv 2207.02543, Algorithm 3 with
+the two-grid cycle of Algorithm 2, P = Phi_r). Workload: 2D plane-stress
+elasticity, Q4 elements on a 512 x 512 grid (526,338 unknowns, 2 x 2 blocks,
+left edge clamped, uniform traction on the right edge), lognormal Young's
+modulus from an 8-term KL field (mean 1, CoV 0.3), nu = 0.3, POD basis k = 20
+from 200 snapshots, a batch of 64 parameter instances sharing one pattern,
+double-float outer PCG with an FP32 preconditioner and FP32 Phi.
+
+One step = per-instance set-up of all 64 instances from FP64 values resident in
+HBM (FP32 conversion, D^-1, K_c = Phi^T K Phi, Cholesky) + the batched solve of
+all 64 to 1e-8. The inputs (4.8 GB of values) are larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one independent replica per GPU (torchrun; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "q4_512"
+TOL = 1e-8
+MAXIT = 5000
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp):
+    """Algorithmic HBM bytes per kernel of the batched iteration (values FP32, vectors
+    double-float 8 B, s/y/D^-1 FP32 4 B, Phi FP32 read once per launch, col_idx
+    once per launch, per-slot scalars and partials negligible)."""
+    P = wl.problem
+    n, nnzb, bs = P.n, P.nnzb, P.bs
+    vals = nnzb * bs * bs * 4
+    pat = nnzb * 4 + (P.n_nodes + 1) * 4
+    phi = n * k_pad * 4
+    per_lane = {  # bytes per active instance-iteration
+        "k_p": n * (4 + 8 + 8),
+        "k_spmv": vals + n * (8 + 8),
+        "k_upd": n * (8 * 4 + 8 * 2),
+        "k_pre": vals + n * (8 + 4),
+        "k_coarse": 0,
+        "k_prol": n * (8 + 4 + 4),
+        "k_post": vals + n * (4 + 8 + 4 + 4),
+    }
+    shared = {"k_p": 0, "k_spmv": pat, "k_upd": 0, "k_pre": pat + phi, "k_coarse": G * Bp * (k_pad + 2) * 8,
+              "k_prol": phi, "k_post": pat}
+    return {name: per_lane[name] * lane_iters + shared[name] * launches for name in per_lane}
+
+
+def run_oracle(mode, inst, timeout=900):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-m", "oracle.timing", WORKLOAD, str(inst), str(mode), str(TOL)],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+def reference_arm(args):
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return 0
+    from synth.problems import Workload
+    from synth.snapshots import pod_basis
+    wl = Workload(WORKLOAD)
+    pod_basis(wl, device="cuda")  # cached POD basis (torch CG snapshots; no solver code)
+    cache = os.path.join(ROOT, "_cache", f"oracle_{WORKLOAD}_iters.json")
+    if os.path.exists(cache):
+        full = json.load(open(cache))
+    else:
+        full = run_oracle("full", 0, timeout=3600)
+        json.dump(full, open(cache, "w"))
+    cores = min(os.cpu_count() or 1, 16)
+    sample_it = 25
+    from concurrent.futures import ThreadPoolExecutor
+
+    def step():
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            outs = list(ex.map(lambda i: run_oracle(sample_it, i), range(cores)))
+        wall = time.perf_counter() - t0
+        per_it = max(o["seconds_per_iteration"] for o in outs)
+        return wall, per_it
+    for _ in range(args.warmup):
+        step()
+    per = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        per.append(step()[1])
+    wall = time.perf_counter() - t0
+    per_it = statistics.mean(per)
+    value = cores / (per_it * full["iterations"])
+    line = {
+        "metric": "solves/s at rel. residual 1e-8 (POD-2G-PCG)", "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": "2D plane-stress Q4 512x512 (526,338 dofs), k=20 POD from 200 snapshots, tol 1e-8"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} single-threaded oracle processes, {sample_it} POD-2G-PCG iterations each "
+                                   f"on distinct instances per step, scaled by the oracle's full iteration count "
+                                   f"({full['iterations']}) for instance 0"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GB300 arm
+def gb300_arm(args):
+    import numpy as np
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2207_02543_gb300 as pkg
+    from synth.problems import Workload
+    from synth.snapshots import pod_basis
+
+    wl = Workload(WORKLOAD)
+    P = wl.problem
+    B = wl.spec.batch
+    t0 = time.time()
+    Phi = pod_basis(wl, device="cuda")
+    t_phi = time.time() - t0
+    # instances of this replica: distinct per rank
+    xis = wl.query_thetas(B, offset=rank * B)
+    vals = wl.values_torch(xis, device="cuda").reshape(B, -1).contiguous()      # FP64, resident in HBM
+    b_dev = torch.from_numpy(wl.rhs(B, offset=rank * B)).cuda()
+    x_dev = torch.empty_like(b_dev)
+    stream = torch.cuda.Stream()
+    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.MIXED_FP32PHI, omega=wl.spec.omega,
+                   max_batch=B, stream=stream.cuda_stream)
+    slots = list(range(B))
+
+    def step():
+        st, sts = s.set_values_batch_dev(slots, vals)
+        assert st == pkg.OK, pkg.strerror(st)
+        iters, rel, status, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=TOL, maxit=MAXIT)
+        assert rc == pkg.OK, (pkg.strerror(rc), status)
+        return iters, rel
+
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 0)):
+        iters, rel = step()
+    sampler = ClockSampler(local)
+    s.kernel_timing(True)
+    l0 = s.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lane_iters = 0
+    for _ in range(args.steps):
+        iters, rel = step()
+        lane_iters += int(np.sum(iters))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = s.launch_count() - l0
+    ktimes = s.kernel_times()
+    s.kernel_timing(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B / (ms / 1e3)
+
+    # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
+    peaks, peak_kind = measured_peaks()
+    G = max(1, min((P.n_nodes * 64 + 255) // 256, 4 * torch.cuda.get_device_properties(local).multi_processor_count))
+    kp = {0: 0}.get(wl.spec.k, [v for v in (0, 8, 16, 24, 32, 40, 48, 64) if v >= wl.spec.k][0])
+    nl = {k: v[1] for k, v in ktimes.items()}
+    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, 64)
+    rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    tot_k = sum(v[0] for v in ktimes.values())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": rates[dom], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": rates[dom] / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                "bytes_per_launch": kb[dom] / max(nl[dom], 1),
+                "ms_per_launch": ktimes[dom][0] / max(nl[dom], 1), "traffic": None,
+                "frac_vs_8TBs": rates[dom] / 8000.0,
+                "all_kernels": {k: {"share": ktimes[k][0] / tot_k, "GBs": round(rates[k], 1),
+                                    "ms_per_launch": ktimes[k][0] / max(nl[k], 1)} for k in ktimes},
+                "spmv_smoother_GBs": (kb["k_spmv"] + kb["k_pre"] + kb["k_post"]) /
+                                     ((ktimes["k_spmv"][0] + ktimes["k_pre"][0] + ktimes["k_post"][0]) / 1e3) / 1e9}
+
+    extra = {}
+    if rank == 0 and world == 1:
+        # end to end through the C ABI with host buffers (values, b in; x out)
+        vals_h = vals.cpu().numpy()
+        b_h = b_dev.cpu().numpy()
+        e2e_steps = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for i in slots:
+                assert s.set_values(i, vals_h[i]) == pkg.OK
+            X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=TOL, maxit=MAXIT)
+            assert rc == pkg.OK
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        extra["e2e"] = {"value": B / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(vals_h.nbytes + b_h.nbytes),
+                        "d2h_bytes_per_step": int(X.nbytes)}
+        # plain FP64 one-at-a-time baseline on the same GPU
+        if not args.no_plain:
+            sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1)
+            nplain = 2
+            times, its = [], []
+            for i in range(nplain):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                assert sp.set_values(0, vals[i]) == pkg.OK
+                xp, itp, relp, stp = sp.solve(0, b_h[i], tol=TOL, maxit=MAXIT)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+                its.append(itp)
+                assert stp == pkg.OK
+            sp.close()
+            extra["plain_fp64"] = {"value": 1.0 / statistics.mean(times), "unit": "solves/s",
+                                   "iters": its, "ratio_batched_over_plain": value / (1.0 / statistics.mean(times))}
+        # serving: Poisson arrivals at ~70% of the batched throughput, continuous batching
+        if not args.no_serve:
+            extra["serving"] = serve_latency(s, pkg, wl, vals_h, b_h, rate=0.7 * value, nreq=args.serve_requests)
+        # CPU baseline: the oracle on a bounded sample (single thread)
+        if not args.no_cpu:
+            try:
+                o = run_oracle(100, 0)
+                it_full = int(iters[0])
+                cpu_val = 1.0 / (o["seconds_per_iteration"] * it_full)
+                extra["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                         "sample": f"instance 0, first 100 POD-2G-PCG iterations of the FP64 oracle "
+                                                   f"(one thread), scaled by the instance's iteration count {it_full}"}
+            except Exception as e:  # noqa: BLE001
+                extra["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                         "sample": f"failed: {e}"[:200]}
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": "solves/s at rel. residual 1e-8 (batched POD-2G-PCG)", "value": value, "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
+            "data": "synthetic",
+            "config": {"workload": "2D plane-stress Q4 512x512 (526,338 dofs, 2x2 BSR), lognormal E (8-term KL, "
+                                   "CoV 0.3), k=20 POD from 200 snapshots, batch 64, tol 1e-8",
+                       "batch": B, "n": P.n, "nnzb": P.nnzb, "k": wl.spec.k, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (4.8 GB FP64 values per step)",
+                       "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
+                       "relres_max": float(np.max(rel)), "phi_setup_s": round(t_phi, 1)},
+            "gpu_launches": int(launches / max(args.steps, 1)) if args.steps else 0,
+            "roofline": roofline, "clocks": clocks,
+        }
+        line.update(extra)
+        line.setdefault("cpu_baseline", None)
+        line.setdefault("e2e", None)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def serve_latency(s, pkg, wl, vals_h, b_h, rate, nreq):
+    import numpy as np
+    rng = np.random.default_rng(3000)
+    gaps = rng.exponential(1.0 / rate, nreq)
+    s.serve_start(max_queue=4 * nreq)
+    tickets = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for i in range(nreq):
+        t_next += gaps[i]
+        while time.perf_counter() < t_next:
+            time.sleep(0.0002)
+        st, t = s.submit(vals_h[i % len(vals_h)], b_h[i % len(b_h)], tol=TOL, maxit=MAXIT)
+        assert st == pkg.OK
+        tickets.append(t)
+    lat = []
+    pending = dict(enumerate(tickets))
+    while pending:
+        for i, t in list(pending.items()):
+            st, r = s.poll(t)
+            if st == pkg.OK:
+                assert r["status"] == pkg.OK
+                lat.append(r["latency_s"])
+                del pending[i]
+        time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    s.serve_stop()
+    lat.sort()
+    return {"requests": nreq, "arrival_rate_per_s": rate, "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "throughput": nreq / wall}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=128)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gb300_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -21,8 +21,10 @@ FP64, MIXED_FP32PHI, MIXED_BF16PHI = 0, 1, 2
 EXPORTS = [
     "pod2g_default_opts", "pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
     "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
-    "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_destroy", "pod2g_strerror",
+    "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_kernel_timing", "pod2g_kernel_times",
+    "pod2g_destroy", "pod2g_strerror",
 ]
+KERNEL_NAMES = ["k_p", "k_spmv", "k_upd", "k_pre", "k_coarse", "k_prol", "k_post"]
 
 
 class Pattern(C.Structure):
@@ -65,6 +67,10 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_info.argtypes = [P, IP, IP, IP, IP]
     lib.pod2g_launch_count.argtypes = [P]
     lib.pod2g_launch_count.restype = C.c_int64
+    lib.pod2g_kernel_timing.argtypes = [P, I]
+    lib.pod2g_kernel_times.argtypes = [P, DP, C.POINTER(C.c_int64)]
+    lib.pod2g_kernel_timing.restype = C.c_int
+    lib.pod2g_kernel_times.restype = C.c_int
     lib.pod2g_destroy.argtypes = [P]
     lib.pod2g_destroy.restype = None
     lib.pod2g_strerror.argtypes = [I]
@@ -143,6 +149,16 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(self._lib.pod2g_launch_count(self.h))
+
+    def kernel_timing(self, on: bool = True) -> int:
+        return self._lib.pod2g_kernel_timing(self.h, int(on))
+
+    def kernel_times(self):
+        """{kernel name: (total ms, timed launches)} of the batched iteration kernels."""
+        ms = np.zeros(7)
+        cnt = np.zeros(7, dtype=np.int64)
+        self._lib.pod2g_kernel_times(self.h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)))
+        return {name: (float(ms[j]), int(cnt[j])) for j, name in enumerate(KERNEL_NAMES)}
 
     # -------------------------------------------------------------- set-up
     def set_values(self, slot: int, values) -> int:

@@ -104,6 +104,7 @@ static void free_all(pod2g_ctx* c) {
     if (c->h_scal64) cudaFreeHost(c->h_scal64);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (auto ev : c->tev) cudaEventDestroy(ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -278,6 +279,20 @@ int pod2g_info(pod2g_t c, int* n, int* nnzb, int* k, int* max_batch) {
 }
 
 int64_t pod2g_launch_count(pod2g_t c) { return c ? (int64_t)c->launches : 0; }
+
+int pod2g_kernel_timing(pod2g_t c, int on) {
+    if (!c || c->serving) return POD2G_INVALID_ARG;
+    return batched_set_timing(c, on);
+}
+
+int pod2g_kernel_times(pod2g_t c, double* ms, int64_t* launches) {
+    if (!c) return POD2G_INVALID_ARG;
+    for (int j = 0; j < 7; ++j) {
+        if (ms) ms[j] = c->kt_ms[j];
+        if (launches) launches[j] = c->kt_n[j];
+    }
+    return POD2G_OK;
+}
 
 static int finish_setup(pod2g_ctx* c, int nslots, const int* slots, int* status) {
     std::vector<int> st(c->B, 0);

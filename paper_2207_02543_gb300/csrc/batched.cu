@@ -556,16 +556,23 @@ static void launch_post(pod2g_ctx* c, Dims D, int want) {
                                               c->d_counters + CNT_POST, c->d_sc);
 }
 
+// Event-record node after a kernel of a captured iteration (timing mode only).
+static int mark(pod2g_ctx* c) {
+    P2G_TRY(pod2g_check_launch(c));
+    if (c->cap_ev) P2G_CUDA(cudaEventRecord(c->cap_ev[c->cap_idx++], c->stream));
+    return POD2G_OK;
+}
+
 // the preconditioner s = AMG(0; K, r, r1, r2) for lanes in state `want`
 static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
     const long long n = c->n;
     if (c->bs == 1) launch_pre<1>(c, D, want);
     else if (c->bs == 2) launch_pre<2>(c, D, want);
     else launch_pre<3>(c, D, want);
-    P2G_TRY(pod2g_check_launch(c));
+    P2G_TRY(mark(c));
     k_coarse<<<c->Bp, POD2G_THREADS, 0, c->stream>>>(D, want, want == SLOT_JOINING, c->d_part, c->d_cpart, c->d_Lc,
                                                      c->d_ec, c->d_sc);
-    P2G_TRY(pod2g_check_launch(c));
+    P2G_TRY(mark(c));
     size_t sm = sizeof(float) * c->Bp * c->kp;
     int gp = std::max(1, std::min(D.G, ceil_div(n * c->Bp, POD2G_THREADS)));
     if (c->pre)
@@ -574,11 +581,11 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
     else
         k_prol<0><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32, c->d_ec, c->d_y32,
                                                         c->d_sc, n);
-    P2G_TRY(pod2g_check_launch(c));
+    P2G_TRY(mark(c));
     if (c->bs == 1) launch_post<1>(c, D, want);
     else if (c->bs == 2) launch_post<2>(c, D, want);
     else launch_post<3>(c, D, want);
-    P2G_TRY(pod2g_check_launch(c));
+    P2G_TRY(mark(c));
     return POD2G_OK;
 }
 
@@ -586,14 +593,15 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
 static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     const long long total = (long long)c->n * c->Bp;
     const int ge = std::max(1, std::min(D.G, ceil_div(total, POD2G_THREADS)));
+    if (c->cap_ev) P2G_CUDA(cudaEventRecord(c->cap_ev[c->cap_idx++], c->stream));
     k_p<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_s32, c->d_pdf, c->d_sc, total);
-    P2G_TRY(pod2g_check_launch(c));
+    P2G_TRY(mark(c));
     LAUNCH_BS(k_spmv, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx, c->d_vals32,
                                                              c->d_pdf, c->d_qdf, c->d_part,
                                                              c->d_counters + CNT_SPMV, c->d_sc));
-    P2G_TRY(pod2g_check_launch(c));
+    P2G_TRY(mark(c));
     k_upd<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_xdf, c->d_rdf, c->d_pdf, c->d_qdf, c->d_sc, total);
-    P2G_TRY(pod2g_check_launch(c));
+    P2G_TRY(mark(c));
     return enqueue_precond(c, D, SLOT_ACTIVE);
 }
 
@@ -655,9 +663,18 @@ static int build_graph(pod2g_ctx* c) {
     if (c->graph_exec) return POD2G_OK;
     Dims D = dims_of(c);
     cudaGraph_t g;
+    if (c->timing && c->tev.empty()) {
+        c->tev.resize((size_t)c->chunk * 8);
+        for (auto& ev : c->tev) P2G_CUDA(cudaEventCreate(&ev));
+    }
     P2G_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int st = POD2G_OK;
-    for (int it = 0; it < c->chunk && st == POD2G_OK; ++it) st = enqueue_iteration(c, D);
+    for (int it = 0; it < c->chunk && st == POD2G_OK; ++it) {
+        c->cap_ev = c->timing ? &c->tev[(size_t)it * 8] : nullptr;
+        c->cap_idx = 0;
+        st = enqueue_iteration(c, D);
+    }
+    c->cap_ev = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != POD2G_OK) return st;
     P2G_CUDA(e);
@@ -676,6 +693,27 @@ int batched_chunk(pod2g_ctx* c) {
     c->launches += (int64_t)7 * c->chunk;
     P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->timing) {
+        for (int it = 0; it < c->chunk; ++it)
+            for (int j = 0; j < 7; ++j) {
+                float ms = 0.f;
+                P2G_CUDA(cudaEventElapsedTime(&ms, c->tev[(size_t)it * 8 + j], c->tev[(size_t)it * 8 + j + 1]));
+                c->kt_ms[j] += ms;
+                c->kt_n[j] += 1;
+            }
+    }
+    return POD2G_OK;
+}
+
+// Per-kernel timing of the captured iterations: on/off (rebuilds the graph).
+int batched_set_timing(pod2g_ctx* c, int on) {
+    if (c->precision == POD2G_FP64) return POD2G_INVALID_ARG;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    c->timing = on != 0;
+    for (int j = 0; j < 8; ++j) { c->kt_ms[j] = 0.0; c->kt_n[j] = 0; }
     return POD2G_OK;
 }
 

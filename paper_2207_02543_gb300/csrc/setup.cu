@@ -159,14 +159,18 @@ __global__ void k_ac(const void* __restrict__ phi_v, const void* __restrict__ W_
         Lout[pr] = 0.5 * (Ac[i * k + j] + Ac[j * k + i]);
     }
     __syncthreads();
-    // right-looking Cholesky in place (lower triangle), FP64
+    // right-looking Cholesky in place (lower triangle), FP64. A pivot below
+    // 64 eps times its original diagonal entry means K_c is numerically singular
+    // (e.g. linearly dependent modes) and is reported as not SPD.
     __shared__ int fail;
+    __shared__ double diag0[POD2G_MAX_K];
     if (threadIdx.x == 0) fail = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) diag0[j] = Lout[j * k + j];
     __syncthreads();
     for (int j = 0; j < k; ++j) {
         if (threadIdx.x == 0) {
             double d = Lout[j * k + j];
-            if (!(d > 0.0) || !isfinite(d)) { fail = 1; d = 1.0; }
+            if (!(d > 64.0 * 2.220446049250313e-16 * diag0[j]) || !isfinite(d)) { fail = 1; d = 1.0; }
             Lout[j * k + j] = sqrt(d);
         }
         __syncthreads();

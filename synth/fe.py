@@ -183,6 +183,37 @@ class StructuredProblem:
             vals[self._diag_blk[cl]] = np.eye(bs)[None]
         return vals
 
+    def values_torch(self, coef):
+        """Batched assembly on a torch device: coef [B, n_el] float64 -> values [B, nnzb, bs, bs].
+
+        Same operations in the same order as values(), so the results are identical."""
+        import torch
+        dev = coef.device
+        Bn = coef.shape[0]
+        bs = self.bs
+        cache = getattr(self, "_torch_maps", None)
+        if cache is None or cache[0] != str(dev):
+            maps = []
+            for emask, blk in self._pair_blk:
+                em = None if emask is None else torch.from_numpy(np.nonzero(emask)[0]).to(dev)
+                maps.append((em, torch.from_numpy(blk).to(dev)))
+            cl = np.nonzero(self.clamped)[0]
+            cache = (str(dev), maps, torch.from_numpy(self._clamp_blocks).to(dev),
+                     torch.from_numpy(self._diag_blk[cl]).to(dev), torch.from_numpy(self.Kref).to(dev))
+            self._torch_maps = cache
+        _, maps, clamp_t, diag_cl_t, Kref = cache
+        vals = torch.zeros((Bn, self.nnzb, bs, bs), dtype=torch.float64, device=dev)
+        for (a, b), (em, blk) in zip(itertools.product(range(2 ** self.dim), repeat=2), maps):
+            if blk.numel() == 0:
+                continue
+            kab = Kref[a * bs:(a + 1) * bs, b * bs:(b + 1) * bs]
+            c = coef if em is None else coef[:, em]
+            vals[:, blk] += c[:, :, None, None] * kab[None, None, :, :]
+        if self.dirichlet == "identity" and clamp_t.numel():
+            vals[:, clamp_t] = 0.0
+            vals[:, diag_cl_t] = torch.eye(bs, dtype=torch.float64, device=dev)
+        return vals
+
     def csr(self, vals: np.ndarray):
         """scipy CSR of the scalar matrix (a library container used by tests and solvers)."""
         import scipy.sparse as sp

@@ -85,6 +85,12 @@ class Workload:
     def values(self, xi: np.ndarray) -> np.ndarray:
         return self.problem.values(self.coef(xi))
 
+    def values_torch(self, xis: np.ndarray, device="cpu"):
+        """Batched values [len(xis), nnzb, bs, bs] (float64 torch tensor), identical to values()."""
+        import torch
+        coef = np.stack([self.coef(xi) for xi in xis])
+        return self.problem.values_torch(torch.from_numpy(coef).to(device))
+
     def snapshot_thetas(self, count: int | None = None) -> np.ndarray:
         from scipy.stats import qmc
         from scipy.special import ndtri

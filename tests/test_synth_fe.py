@@ -200,3 +200,13 @@ def test_workload_seeds_are_deterministic():
     assert np.array_equal(a, b)
     th = wl.snapshot_thetas()
     assert th.shape == (SPECS["q4_16"].n_snap, SPECS["q4_16"].m)
+
+
+@pytest.mark.parametrize("name", ["q1_16", "q4_16", "hex8_8"])
+def test_batched_torch_assembly_identical(name):
+    torch = pytest.importorskip("torch")
+    wl = Workload(name)
+    xis = wl.query_thetas(3)
+    V = wl.values_torch(xis).numpy()
+    for i, xi in enumerate(xis):
+        assert np.array_equal(V[i], wl.values(xi))
