@@ -194,9 +194,9 @@ def gb300_arm(args):
     from synth.problems import Workload
     from synth.snapshots import pod_basis
 
-    wl = Workload(WORKLOAD)
+    wl = Workload(args.workload)
     P = wl.problem
-    B = wl.spec.batch
+    B = args.batch or wl.spec.batch
     t0 = time.time()
     Phi = pod_basis(wl, device="cuda")
     t_phi = time.time() - t0
@@ -250,10 +250,11 @@ def gb300_arm(args):
 
     # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
     peaks, peak_kind = measured_peaks()
-    G = max(1, min((P.n_nodes * 64 + 255) // 256, 4 * torch.cuda.get_device_properties(local).multi_processor_count))
+    Bp = 1 << (B - 1).bit_length()
+    G = max(1, min((P.n_nodes * Bp + 255) // 256, 4 * torch.cuda.get_device_properties(local).multi_processor_count))
     kp = {0: 0}.get(wl.spec.k, [v for v in (0, 8, 16, 24, 32, 40, 48, 64) if v >= wl.spec.k][0])
     nl = {k: v[1] for k, v in ktimes.items()}
-    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, 64)
+    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp)
     rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     tot_k = sum(v[0] for v in ktimes.values())
@@ -382,6 +383,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=128)
+    ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling of smaller cases)")
+    ap.add_argument("--batch", type=int, default=0, help="instances per step (default: the workload's batch)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -5,10 +5,19 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void pod2g_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+void pod2g_trace(const char* file, int line, int status) {
+    static const bool on = getenv("POD2G_DEBUG") != nullptr;
+    if (on)
+        fprintf(stderr, "pod2g: %s:%d -> status %d (%s)\n", file, line, status,
+                status == POD2G_CUDA_ERROR ? cudaGetErrorString(g_last_cuda) : "");
+}
 
 int pod2g_check_launch(pod2g_ctx* c) {
     c->launches++;
@@ -340,7 +349,12 @@ static int check_slots(pod2g_ctx* c, int nslots, const int* slots) {
     std::vector<char> seen(c->B, 0);
     for (int i = 0; i < nslots; ++i) {
         int s = slots[i];
-        if (s < 0 || s >= c->B || seen[s] || !c->setup_ok[s]) return POD2G_INVALID_ARG;
+        if (s < 0 || s >= c->B || seen[s] || !c->setup_ok[s]) {
+            if (getenv("POD2G_DEBUG"))
+                fprintf(stderr, "pod2g: slot %d (index %d) rejected: B=%d seen=%d setup_ok=%d\n", s, i, c->B,
+                        (s >= 0 && s < c->B) ? (int)seen[s] : -1, (s >= 0 && s < c->B) ? c->setup_ok[s] : -1);
+            return POD2G_INVALID_ARG;
+        }
         seen[s] = 1;
     }
     return POD2G_OK;

@@ -37,6 +37,22 @@ struct Dims {
     double omega;
 };
 
+// p[g0*stride] + ... + p[(g1-1)*stride], added in increasing g (so the result is
+// that of the plain serial loop); loads are issued eight at a time.
+__device__ __forceinline__ double ordered_sum(const double* __restrict__ p, int g0, int g1, long long stride) {
+    double s = 0.0;
+    int g = g0;
+    for (; g + 8 <= g1; g += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = p[(long long)(g + u) * stride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; g < g1; ++g) s += p[(long long)g * stride];
+    return s;
+}
+
 // sum over the threads of this CTA that own `lane` (thread t owns lane t % Bp),
 // in thread order; result to out[lane] for lane < Bp. smem must hold blockDim doubles.
 __device__ __forceinline__ void cta_lane_sum(double v, int Bp, double* smem, double* out) {
@@ -56,8 +72,7 @@ __device__ __forceinline__ double grid_lane_total(const double* part, int G, int
     const int Q = blockDim.x / Bp;
     const int b = threadIdx.x % Bp, q = threadIdx.x / Bp;
     const int g0 = (int)((long long)G * q / Q), g1 = (int)((long long)G * (q + 1) / Q);
-    double s = 0.0;
-    for (int g = g0; g < g1; ++g) s += part[(long long)g * stride + b];
+    double s = ordered_sum(part + b, g0, g1, stride);
     __syncthreads();
     smem[threadIdx.x] = s;
     __syncthreads();
@@ -340,14 +355,19 @@ __global__ void k_coarse(Dims D, int want, int init, const double* __restrict__ 
     __shared__ int go;
     const int b = blockIdx.x;
     if (sc[b].state != want) return;
-    // ||r||^2 over CTAs, fixed order
-    double s = 0.0;
-    for (int g = threadIdx.x; g < D.G; g += blockDim.x) s += part[(long long)g * D.Bp * 2 + b];
-    smem[threadIdx.x] = s;
-    __syncthreads();
+    // ||r||^2 over CTAs: contiguous ranges per thread, then a fixed tree
+    {
+        const int T = blockDim.x;
+        const int g0 = (int)((long long)D.G * threadIdx.x / T), g1 = (int)((long long)D.G * (threadIdx.x + 1) / T);
+        smem[threadIdx.x] = ordered_sum(part + b, g0, g1, (long long)D.Bp * 2);
+        __syncthreads();
+        for (int h = T / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) smem[threadIdx.x] += smem[threadIdx.x + h];
+            __syncthreads();
+        }
+    }
     if (threadIdx.x == 0) {
-        double rr = 0.0;
-        for (int t = 0; t < (int)blockDim.x; ++t) rr += smem[t];
+        double rr = smem[0];
         SlotScalars& S = sc[b];
         S.rr = rr;
         go = 1;
@@ -366,7 +386,7 @@ __global__ void k_coarse(Dims D, int want, int init, const double* __restrict__ 
     double cs = 0.0;
     if (q < Q) {
         const int g0 = (int)((long long)D.G * q / Q), g1 = (int)((long long)D.G * (q + 1) / Q);
-        for (int g = g0; g < g1; ++g) cs += cpart[((long long)g * D.Bp + b) * kp + m];
+        cs = ordered_sum(cpart + (long long)b * kp + m, g0, g1, (long long)D.Bp * kp);
     }
     __syncthreads();
     smem[threadIdx.x] = cs;
@@ -405,14 +425,14 @@ template <int PRE>
 __global__ void k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restrict__ r,
                        const float* __restrict__ phi, const float* __restrict__ ec, float* __restrict__ y,
                        const SlotScalars* __restrict__ sc, long long n) {
-    extern __shared__ float s_ec[];  // [Bp][kp]
-    for (int e = threadIdx.x; e < D.Bp * D.kp; e += blockDim.x) s_ec[e] = ec[e];
+    extern __shared__ float s_ec[];  // [Bp][kp + 1] (odd row stride: no bank conflicts across slots)
+    for (int e = threadIdx.x; e < D.Bp * D.kp; e += blockDim.x) s_ec[(e / D.kp) * (D.kp + 1) + e % D.kp] = ec[e];
     __syncthreads();
     const int lane = threadIdx.x & (D.Bp - 1);
     if (sc[lane].state != want) return;
     const float w = (float)D.omega;
     const int kp = D.kp;
-    const float* el = s_ec + lane * kp;
+    const float* el = s_ec + lane * (kp + 1);
     const long long items = n << D.lgBp;
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
          it += (long long)gridDim.x * blockDim.x) {
@@ -559,7 +579,7 @@ static void launch_post(pod2g_ctx* c, Dims D, int want) {
 // Event-record node after a kernel of a captured iteration (timing mode only).
 static int mark(pod2g_ctx* c) {
     P2G_TRY(pod2g_check_launch(c));
-    if (c->cap_ev) P2G_CUDA(cudaEventRecord(c->cap_ev[c->cap_idx++], c->stream));
+    if (c->cap_ev) P2G_CUDA(cudaEventRecordWithFlags(c->cap_ev[c->cap_idx++], c->stream, cudaEventRecordExternal));
     return POD2G_OK;
 }
 
@@ -573,7 +593,7 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
     k_coarse<<<c->Bp, POD2G_THREADS, 0, c->stream>>>(D, want, want == SLOT_JOINING, c->d_part, c->d_cpart, c->d_Lc,
                                                      c->d_ec, c->d_sc);
     P2G_TRY(mark(c));
-    size_t sm = sizeof(float) * c->Bp * c->kp;
+    size_t sm = sizeof(float) * c->Bp * (c->kp + 1);
     int gp = std::max(1, std::min(D.G, ceil_div(n * c->Bp, POD2G_THREADS)));
     if (c->pre)
         k_prol<1><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32, c->d_ec, c->d_y32,
@@ -593,7 +613,7 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
 static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     const long long total = (long long)c->n * c->Bp;
     const int ge = std::max(1, std::min(D.G, ceil_div(total, POD2G_THREADS)));
-    if (c->cap_ev) P2G_CUDA(cudaEventRecord(c->cap_ev[c->cap_idx++], c->stream));
+    if (c->cap_ev) P2G_CUDA(cudaEventRecordWithFlags(c->cap_ev[c->cap_idx++], c->stream, cudaEventRecordExternal));
     k_p<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_s32, c->d_pdf, c->d_sc, total);
     P2G_TRY(mark(c));
     LAUNCH_BS(k_spmv, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx, c->d_vals32,

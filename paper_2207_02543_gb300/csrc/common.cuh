@@ -148,6 +148,7 @@ struct ServeRequest {
         cudaError_t e__ = (call);                                               \
         if (e__ != cudaSuccess) {                                               \
             pod2g_set_last_cuda_error(e__);                                     \
+            pod2g_trace(__FILE__, __LINE__, POD2G_CUDA_ERROR);                  \
             return POD2G_CUDA_ERROR;                                            \
         }                                                                       \
     } while (0)
@@ -155,8 +156,14 @@ struct ServeRequest {
 #define P2G_TRY(call)                                                           \
     do {                                                                        \
         int s__ = (call);                                                       \
-        if (s__ != POD2G_OK) return s__;                                        \
+        if (s__ != POD2G_OK) {                                                  \
+            pod2g_trace(__FILE__, __LINE__, s__);                               \
+            return s__;                                                         \
+        }                                                                       \
     } while (0)
+
+// With POD2G_DEBUG set in the environment, failing calls are traced to stderr.
+void pod2g_trace(const char* file, int line, int status);
 
 void pod2g_set_last_cuda_error(cudaError_t e);
 int pod2g_check_launch(pod2g_ctx* c);  // counts a launch, checks cudaGetLastError
