@@ -67,6 +67,7 @@ extern "C" {
 #define POD2G_TIMEOUT        8  /* a bounded device or host wait expired */
 #define POD2G_NONFINITE      9  /* NaN or Inf in an input or an iterate */
 #define POD2G_PENDING       10  /* pod2g_poll: request not finished yet */
+#define POD2G_TOO_LARGE     11  /* pod2g_solve_noalloc: size beyond its fixed scratch capacity */
 
 /* precision modes */
 #define POD2G_FP64           0
@@ -174,6 +175,46 @@ int pod2g_kernel_times(pod2g_t ctx, double* ms, int64_t* launches);
 
 /* Free all device memory of the context. NULL is ignored. */
 void pod2g_destroy(pod2g_t ctx);
+
+/* Solve without allocating device memory (the paper has no counterpart: this is
+ * a deployment variant of pod2g_solve on a POD2G_FP64 context).
+ *
+ * For callers that cannot call cudaMalloc: code whose device memory is owned by
+ * another allocator (a framework's caching allocator, a pool reserved at start-up),
+ * callers that must not trigger the device-wide synchronisation that cudaMalloc /
+ * cudaFree can imply, and embedders that only hand over buffers they already own.
+ * It runs the same kernels as pod2g_solve on an FP64 context (same results), but
+ * every scratch buffer lives in one file-scope static device array of about
+ * 10.5 MB, which each GPU that loads the library holds until the process exits.
+ * Nothing is allocated or freed; no context is needed.
+ *
+ * Inputs (device pointers, read only): the block-CSR pattern (row_ptr_dev
+ * [n_brows+1], col_idx_dev [nnzb], sorted columns, diagonal present), values_dev
+ * (nnzb*bs*bs doubles, row-major blocks), phi_dev (n*k doubles, column-major, may
+ * be NULL when k = 0), b_dev and x0_dev (n doubles; x0_dev NULL = zero). opts:
+ * omega, pre, post, beta_pr are used (NULL = defaults); precision, max_batch,
+ * hbm_budget, chunk and stream are ignored. Output: x_dev (n doubles, device);
+ * iters, relres, status (host, may be NULL) as for pod2g_solve. stream: the
+ * cudaStream_t to run on (NULL = the legacy default stream).
+ *
+ * Limits: n = n_brows*bs <= POD2G_NOALLOC_MAX_N and k <= POD2G_NOALLOC_MAX_K;
+ * larger sizes return POD2G_TOO_LARGE before any device work. An invalid pattern
+ * returns POD2G_INVALID_ARG.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the
+ * device address of the static array; make that first call before any CUDA stream
+ * capture. Every call shares the array and overwrites what the previous call left
+ * there; the counters that must start at zero are cleared at the start of each
+ * call. Calls that overlap on the GPU would race on the array: the library
+ * serialises calls made from one process with a lock, and each call returns only
+ * after its GPU work has finished. Returns the solve status (POD2G_OK when
+ * converged), or an error code. */
+#define POD2G_NOALLOC_MAX_N 16384
+#define POD2G_NOALLOC_MAX_K 32
+int pod2g_solve_noalloc(int32_t n_brows, int32_t bs, int32_t nnzb, const int32_t* row_ptr_dev,
+                        const int32_t* col_idx_dev, const double* values_dev, const double* phi_dev, int k,
+                        const pod2g_opts* opts, const double* b_dev, const double* x0_dev, double tol,
+                        int maxit, double* x_dev, int* iters, double* relres, int* status, void* stream);
 
 /* Static message for a status code. Never NULL. */
 const char* pod2g_strerror(int status);

@@ -22,8 +22,10 @@ EXPORTS = [
     "pod2g_default_opts", "pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
     "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
     "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_kernel_timing", "pod2g_kernel_times",
-    "pod2g_destroy", "pod2g_strerror",
+    "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc",
 ]
+NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
+TOO_LARGE = 11
 KERNEL_NAMES = ["k_p", "k_spmv", "k_upd", "k_pre", "k_coarse", "k_prol", "k_post"]
 
 
@@ -71,6 +73,9 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_kernel_times.argtypes = [P, DP, C.POINTER(C.c_int64)]
     lib.pod2g_kernel_timing.restype = C.c_int
     lib.pod2g_kernel_times.restype = C.c_int
+    lib.pod2g_solve_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, I, C.POINTER(Opts), P, P, D, I,
+                                        P, IP, DP, IP, P]
+    lib.pod2g_solve_noalloc.restype = C.c_int
     lib.pod2g_destroy.argtypes = [P]
     lib.pod2g_destroy.restype = None
     lib.pod2g_strerror.argtypes = [I]
@@ -251,3 +256,23 @@ class Solver:
 
     def serve_stop(self):
         return self._lib.pod2g_serve_stop(self.h)
+
+
+def solve_noalloc(row_ptr_dev, col_idx_dev, bs, values_dev, phi_dev, k, b_dev, x_dev, x0_dev=None, tol=1e-8,
+                  maxit=1000, omega=2.0 / 3.0, pre=1, post=1, beta_pr=False, stream=None):
+    """pod2g_solve_noalloc: FP64 solve with no device allocation. All arrays are CUDA tensors
+    (row_ptr/col_idx int32, values/phi/b/x0/x float64; phi column-major [k][n] flattened).
+    Returns (rc, iters, relres, status)."""
+    lib = load_library()
+    o = Opts()
+    lib.pod2g_default_opts(C.byref(o))
+    o.omega, o.pre, o.post, o.beta_pr, o.precision = omega, pre, post, int(beta_pr), FP64
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    st = C.c_int(0)
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    nb = row_ptr_dev.numel() - 1
+    rc = lib.pod2g_solve_noalloc(nb, bs, col_idx_dev.numel(), ptr(row_ptr_dev), ptr(col_idx_dev), ptr(values_dev),
+                                 ptr(phi_dev), k, C.byref(o), ptr(b_dev), ptr(x0_dev), tol, maxit, ptr(x_dev),
+                                 C.byref(it), C.byref(rr), C.byref(st), C.c_void_p(stream) if stream else None)
+    return rc, it.value, rr.value, st.value

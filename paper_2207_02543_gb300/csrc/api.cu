@@ -97,6 +97,7 @@ const char* pod2g_strerror(int s) {
         case POD2G_TIMEOUT: return "timeout";
         case POD2G_NONFINITE: return "non-finite value";
         case POD2G_PENDING: return "pending";
+        case POD2G_TOO_LARGE: return "size exceeds the fixed scratch capacity of pod2g_solve_noalloc";
         default: return "unknown status";
     }
 }
