@@ -106,13 +106,14 @@ def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp):
         "k_p": n * (4 + 8 + 8),
         "k_spmv": vals + n * (8 + 8),
         "k_upd": n * (8 * 4 + 8 * 2),
-        "k_pre": vals + n * (8 + 4),
+        "k_smooth1": vals + n * (8 + 4 + 4),
+        "k_restrict": n * 4,
         "k_coarse": 0,
         "k_prol": n * (8 + 4 + 4),
         "k_post": vals + n * (4 + 8 + 4 + 4),
     }
-    shared = {"k_p": 0, "k_spmv": pat, "k_upd": 0, "k_pre": pat + phi, "k_coarse": G * Bp * (k_pad + 2) * 8,
-              "k_prol": phi, "k_post": pat}
+    shared = {"k_p": 0, "k_spmv": pat, "k_upd": 0, "k_smooth1": pat, "k_restrict": phi,
+              "k_coarse": G // 8 * Bp * (k_pad + 2) * 8, "k_prol": phi, "k_post": pat}
     return {name: per_lane[name] * lane_iters + shared[name] * launches for name in per_lane}
 
 
@@ -265,8 +266,8 @@ def gb300_arm(args):
                 "frac_vs_8TBs": rates[dom] / 8000.0,
                 "all_kernels": {k: {"share": ktimes[k][0] / tot_k, "GBs": round(rates[k], 1),
                                     "ms_per_launch": ktimes[k][0] / max(nl[k], 1)} for k in ktimes},
-                "spmv_smoother_GBs": (kb["k_spmv"] + kb["k_pre"] + kb["k_post"]) /
-                                     ((ktimes["k_spmv"][0] + ktimes["k_pre"][0] + ktimes["k_post"][0]) / 1e3) / 1e9}
+                "spmv_smoother_GBs": (kb["k_spmv"] + kb["k_smooth1"] + kb["k_post"]) /
+                                     ((ktimes["k_spmv"][0] + ktimes["k_smooth1"][0] + ktimes["k_post"][0]) / 1e3) / 1e9}
 
     extra = {}
     if rank == 0 and world == 1:

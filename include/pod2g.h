@@ -164,12 +164,12 @@ int pod2g_info(pod2g_t ctx, int* n, int* nnzb, int* k, int* max_batch);
 int64_t pod2g_launch_count(pod2g_t ctx);
 
 /* Per-kernel timing of the batched PCG iteration (mixed contexts only). With
- * on != 0, CUDA events are recorded around each of the 7 kernels of every
+ * on != 0, CUDA events are recorded around each of the 8 kernels of every
  * iteration inside the CUDA graph, and accumulated after each graph launch;
  * switching resets the totals. pod2g_kernel_times copies, for kernel j =
- * 0..6 (p update, K p, x/r update, pre-smoothing + restriction, coarse solve,
+ * 0..7 (p update, K p, x/r update, pre-smoothing, restriction, coarse solve,
  * prolongation, post-smoothing), the total milliseconds ms[j] and the number of
- * timed launches launches[j] (arrays of 7; either may be NULL). */
+ * timed launches launches[j] (arrays of 8; either may be NULL). */
 int pod2g_kernel_timing(pod2g_t ctx, int on);
 int pod2g_kernel_times(pod2g_t ctx, double* ms, int64_t* launches);
 

@@ -26,7 +26,7 @@ EXPORTS = [
 ]
 NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
 TOO_LARGE = 11
-KERNEL_NAMES = ["k_p", "k_spmv", "k_upd", "k_pre", "k_coarse", "k_prol", "k_post"]
+KERNEL_NAMES = ["k_p", "k_spmv", "k_upd", "k_smooth1", "k_restrict", "k_coarse", "k_prol", "k_post"]
 
 
 class Pattern(C.Structure):
@@ -160,8 +160,8 @@ class Solver:
 
     def kernel_times(self):
         """{kernel name: (total ms, timed launches)} of the batched iteration kernels."""
-        ms = np.zeros(7)
-        cnt = np.zeros(7, dtype=np.int64)
+        ms = np.zeros(8)
+        cnt = np.zeros(8, dtype=np.int64)
         self._lib.pod2g_kernel_times(self.h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)))
         return {name: (float(ms[j]), int(cnt[j])) for j, name in enumerate(KERNEL_NAMES)}
 

@@ -297,7 +297,7 @@ int pod2g_kernel_timing(pod2g_t c, int on) {
 
 int pod2g_kernel_times(pod2g_t c, double* ms, int64_t* launches) {
     if (!c) return POD2G_INVALID_ARG;
-    for (int j = 0; j < 7; ++j) {
+    for (int j = 0; j < 8; ++j) {
         if (ms) ms[j] = c->kt_ms[j];
         if (launches) launches[j] = c->kt_n[j];
     }

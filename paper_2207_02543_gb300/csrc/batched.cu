@@ -17,23 +17,39 @@
 // preconditioner (smoothing, restriction, prolongation) is FP32; per-slot
 // scalars, cross-CTA sums and the coarse Cholesky solve are FP64.
 //
-// One PCG iteration = 7 kernels, captured `chunk` times in one CUDA graph:
+// The sparse row kernels are memory-latency bound unless many loads are in
+// flight: each thread fetches the column indices, values and gathered vector
+// entries of UNROLL blocks before using any of them, and the grids fill every
+// SM. Per-slot partial sums are first combined across an 8-CTA thread-block
+// cluster through distributed shared memory, so the last cluster to finish sums
+// G/8 partial rows instead of G.
+//
+// One PCG iteration = 8 kernels, captured `chunk` times in one CUDA graph:
 //   k_p      p = s + beta p
-//   k_spmv   q = K p, p^T q             (last CTA: alpha = r^T s / p^T q, maxit, breakdown)
+//   k_spmv   q = K p, p^T q             (last cluster: alpha = r^T s / p^T q, maxit, breakdown)
 //   k_upd    x += alpha p, r -= alpha q
-//   k_pre    y1 = omega D^-1 r, r1 = r - K y1, partials of Phi^T r1 and ||r||^2
-//   k_coarse per slot: ||r|| test, c = Phi^T r1, e_c = L^-T L^-1 c
+//   k_smooth1 y1 = omega D^-1 r, r1 = r - K y1 (stored), partials of ||r||^2
+//   k_restrict partials of c = Phi^T r1
+//   k_coarse per slot: ||r|| test, c, e_c = L^-T L^-1 c
 //   k_prol   y2 = y1 + Phi e_c
-//   k_post   s = y2 + omega D^-1 (r - K y2), r^T s  (last CTA: beta)
+//   k_post   s = y2 + omega D^-1 (r - K y2), r^T s  (last cluster: beta)
 #include "common.cuh"
+
+#include <cooperative_groups.h>
 
 #include <chrono>
 #include <cmath>
 
+namespace cg = cooperative_groups;
+
+#define CLUSTER 8   // CTAs per thread-block cluster of the row kernels
+#define UNROLL 3    // blocks of a row fetched ahead
+
 namespace {
 
 struct Dims {
-    int nb, Bp, lgBp, k, kp, G;
+    int nb, Bp, lgBp, k, kp, G, NP;  // NP = G / CLUSTER partial-sum rows of the row kernels
+    int NPc;                         // partial-sum rows of the restriction
     double omega;
 };
 
@@ -53,37 +69,89 @@ __device__ __forceinline__ double ordered_sum(const double* __restrict__ p, int 
     return s;
 }
 
-// sum over the threads of this CTA that own `lane` (thread t owns lane t % Bp),
-// in thread order; result to out[lane] for lane < Bp. smem must hold blockDim doubles.
-__device__ __forceinline__ void cta_lane_sum(double v, int Bp, double* smem, double* out) {
+// Per-slot CTA sum: thread t contributes v to slot t % Bp; the sums (in thread
+// order) land in s_out[slot]. Ends with a barrier.
+__device__ __forceinline__ void cta_lane_sum(double v, int Bp, double* s_tmp, double* s_out) {
     __syncthreads();
-    smem[threadIdx.x] = v;
+    s_tmp[threadIdx.x] = v;
     __syncthreads();
     if ((int)threadIdx.x < Bp) {
         double s = 0.0;
-        for (int t = threadIdx.x; t < (int)blockDim.x; t += Bp) s += smem[t];
-        out[threadIdx.x] = s;
+        for (int t = threadIdx.x; t < (int)blockDim.x; t += Bp) s += s_tmp[t];
+        s_out[threadIdx.x] = s;
     }
+    __syncthreads();
 }
 
-// total over CTAs g = 0..G-1 of part[g * stride + lane] (fixed order), computed by
-// all threads of one CTA; returns the total in threads t < Bp (t = lane).
-__device__ __forceinline__ double grid_lane_total(const double* part, int G, int stride, int Bp, double* smem) {
+// The cluster's rank-0 CTA sums s_vals[0..nv) of all CTAs of its cluster (rank
+// order, read through distributed shared memory) into out[0..nv).
+__device__ __forceinline__ void cluster_store(const double* s_vals, int nv, double* out) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (cl.block_rank() == 0) {
+        const int nr = (int)cl.num_blocks();
+        for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+            double s = 0.0;
+            for (int r = 0; r < nr; ++r) s += cl.map_shared_rank(const_cast<double*>(s_vals), r)[e];
+            out[e] = s;
+        }
+    }
+    cl.sync();
+}
+
+// After cluster_store: true in exactly one CTA, the rank-0 CTA of the last
+// cluster to arrive, which may then read all NP partial rows. No CTA waits on
+// another cluster, so nothing can hang. The counter is reset by that CTA.
+__device__ __forceinline__ bool last_cluster_arrive(unsigned* counter, int nclusters) {
+    __shared__ bool am_last;
+    if (cg::this_cluster().block_rank() != 0) return false;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(counter, 1u);
+        am_last = (prev == (unsigned)nclusters - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+// total over partial rows g = 0..NP-1 of part[g * stride + slot] (fixed order),
+// computed by all threads of one CTA; the total is returned in threads t < Bp.
+__device__ __forceinline__ double grid_lane_total(const double* part, int NP, int stride, int Bp, double* s_tmp) {
     const int Q = blockDim.x / Bp;
     const int b = threadIdx.x % Bp, q = threadIdx.x / Bp;
-    const int g0 = (int)((long long)G * q / Q), g1 = (int)((long long)G * (q + 1) / Q);
+    const int g0 = (int)((long long)NP * q / Q), g1 = (int)((long long)NP * (q + 1) / Q);
     double s = ordered_sum(part + b, g0, g1, stride);
     __syncthreads();
-    smem[threadIdx.x] = s;
+    s_tmp[threadIdx.x] = s;
     __syncthreads();
     double tot = 0.0;
     if ((int)threadIdx.x < Bp)
-        for (int qq = 0; qq < Q; ++qq) tot += smem[qq * Bp + threadIdx.x];
+        for (int qq = 0; qq < Q; ++qq) tot += s_tmp[qq * Bp + threadIdx.x];
     return tot;
 }
 
 __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 df_of(float a) { return make_float2(a, 0.f); }
+
+// Prefetching loop over the blocks b0..b1 of one block row: for each group of
+// UNROLL blocks, `fetch(u, blk, j)` issues the loads of block blk (column j) into
+// slot u, then `use(u)` consumes them. Blocks past the row end are skipped.
+template <class Fetch, class Use>
+__device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, int b0, int b1, Fetch fetch, Use use) {
+    for (int blk0 = b0; blk0 < b1; blk0 += UNROLL) {
+        int jj[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) jj[u] = (blk0 + u < b1) ? __ldg(col_idx + blk0 + u) : -1;
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (jj[u] >= 0) fetch(u, blk0 + u, jj[u]);
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (jj[u] >= 0) use(u);
+    }
+}
 
 // ---------------------------------------------------------------------------- load / store / residual
 // Joining lanes: b -> bdf, x0 -> xdf (zero if absent), p = q = 0.
@@ -121,11 +189,12 @@ __global__ void k_store(double* __restrict__ x, const int* __restrict__ slots, i
 // sets tol2 = tol^2 ||b||^2 (b = 0 or non-finite -> DONE). final: sums
 // ||b - K x||^2 into relres.
 template <int BS>
-__global__ void __launch_bounds__(POD2G_THREADS) k_resid(Dims D, int final_mode, const int* __restrict__ mask,
-    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, const float* __restrict__ vals,
-    const float2* __restrict__ x, const float2* __restrict__ b, float2* __restrict__ r, double* part,
-    unsigned* counter, SlotScalars* sc) {
-    __shared__ double smem[POD2G_THREADS];
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __restrict__ row_ptr,
+        const int32_t* __restrict__ col_idx, const float* __restrict__ vals, const float2* __restrict__ x,
+        const float2* __restrict__ b, float2* __restrict__ r, double* part, unsigned* counter, SlotScalars* sc) {
+    __shared__ double s_tmp[POD2G_THREADS];
+    __shared__ double s_out[2 * POD2G_MAX_BP];
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = mask[lane] != 0;
     float bh = 0.f, bl = 0.f, rh = 0.f, rl = 0.f;
@@ -137,18 +206,23 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_resid(Dims D, int final_mode,
             float ah[BS], al[BS];
 #pragma unroll
             for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
-            for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
-                const int j = col_idx[blk];
-                float2 xj[BS];
+            float2 xj[UNROLL][BS];
+            float v[UNROLL][BS * BS];
+            row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+                [&](int u, int blk, int j) {
 #pragma unroll
-                for (int cc = 0; cc < BS; ++cc) xj[cc] = x[((long long)j * BS + cc) * D.Bp + lane];
+                    for (int cc = 0; cc < BS; ++cc) xj[u][cc] = x[((long long)j * BS + cc) * D.Bp + lane];
+                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                for (int a = 0; a < BS; ++a)
+                    for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                },
+                [&](int u) {
 #pragma unroll
-                    for (int cc = 0; cc < BS; ++cc)
-                        df_acc_fma(ah[a], al[a], vals[((long long)blk * BS * BS + a * BS + cc) * D.Bp + lane],
-                                   xj[cc].x, xj[cc].y);
-            }
+                    for (int a = 0; a < BS; ++a)
+#pragma unroll
+                        for (int cc = 0; cc < BS; ++cc)
+                            df_acc_fma(ah[a], al[a], v[u][a * BS + cc], xj[u][cc].x, xj[u][cc].y);
+                });
 #pragma unroll
             for (int a = 0; a < BS; ++a) {
                 const long long o = ((long long)i * BS + a) * D.Bp + lane;
@@ -160,12 +234,12 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_resid(Dims D, int final_mode,
             }
         }
     }
-    double* pg = part + (long long)blockIdx.x * D.Bp * 2;
-    cta_lane_sum((double)bh + (double)bl, D.Bp, smem, pg);
-    cta_lane_sum((double)rh + (double)rl, D.Bp, smem, pg + D.Bp);
-    if (!last_cta_arrive(counter)) return;
-    double bb = grid_lane_total(part, D.G, 2 * D.Bp, D.Bp, smem);
-    double rr = grid_lane_total(part + D.Bp, D.G, 2 * D.Bp, D.Bp, smem);
+    cta_lane_sum((double)bh + (double)bl, D.Bp, s_tmp, s_out);
+    cta_lane_sum((double)rh + (double)rl, D.Bp, s_tmp, s_out + D.Bp);
+    cluster_store(s_out, 2 * D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
+    if (!last_cluster_arrive(counter, D.NP)) return;
+    double bb = grid_lane_total(part, D.NP, 2 * D.Bp, D.Bp, s_tmp);
+    double rr = grid_lane_total(part + D.Bp, D.NP, 2 * D.Bp, D.Bp, s_tmp);
     if ((int)threadIdx.x < D.Bp && mask[threadIdx.x]) {
         SlotScalars& s = sc[threadIdx.x];
         if (final_mode) {
@@ -180,7 +254,7 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_resid(Dims D, int final_mode,
             }
         }
     }
-    last_cta_reset(counter);
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // ---------------------------------------------------------------------------- PCG kernels
@@ -195,12 +269,14 @@ __global__ void k_p(Dims D, int want, const float* __restrict__ s, float2* __res
         p[e] = df_add(df_of(s[e]), df_mul(beta, p[e]));
 }
 
-// q = K p (double-float), partial p^T q; last CTA: alpha per slot.
+// q = K p (double-float), partial p^T q; last cluster: alpha per slot.
 template <int BS>
-__global__ void __launch_bounds__(POD2G_THREADS) k_spmv(Dims D, int want,
-    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, const float* __restrict__ vals,
-    const float2* __restrict__ p, float2* __restrict__ q, double* part, unsigned* counter, SlotScalars* sc) {
-    __shared__ double smem[POD2G_THREADS];
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+       const float* __restrict__ vals, const float2* __restrict__ p, float2* __restrict__ q, double* part,
+       unsigned* counter, SlotScalars* sc) {
+    __shared__ double s_tmp[POD2G_THREADS];
+    __shared__ double s_out[POD2G_MAX_BP];
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float dh = 0.f, dl = 0.f;
@@ -212,19 +288,23 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_spmv(Dims D, int want,
             float ah[BS], al[BS];
 #pragma unroll
             for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
-            const int b0 = row_ptr[i], b1 = row_ptr[i + 1];
-            for (int blk = b0; blk < b1; ++blk) {
-                const int j = col_idx[blk];
-                float2 pj[BS];
+            float2 pj[UNROLL][BS];
+            float v[UNROLL][BS * BS];
+            row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+                [&](int u, int blk, int j) {
 #pragma unroll
-                for (int cc = 0; cc < BS; ++cc) pj[cc] = p[((long long)j * BS + cc) * D.Bp + lane];
-                const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+                    for (int cc = 0; cc < BS; ++cc) pj[u][cc] = p[((long long)j * BS + cc) * D.Bp + lane];
+                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                for (int a = 0; a < BS; ++a)
+                    for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                },
+                [&](int u) {
 #pragma unroll
-                    for (int cc = 0; cc < BS; ++cc)
-                        df_acc_fma(ah[a], al[a], vb[(a * BS + cc) * D.Bp], pj[cc].x, pj[cc].y);
-            }
+                    for (int a = 0; a < BS; ++a)
+#pragma unroll
+                        for (int cc = 0; cc < BS; ++cc)
+                            df_acc_fma(ah[a], al[a], v[u][a * BS + cc], pj[u][cc].x, pj[u][cc].y);
+                });
 #pragma unroll
             for (int a = 0; a < BS; ++a) {
                 const long long o = ((long long)i * BS + a) * D.Bp + lane;
@@ -237,9 +317,10 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_spmv(Dims D, int want,
             }
         }
     }
-    cta_lane_sum((double)dh + (double)dl, D.Bp, smem, part + (long long)blockIdx.x * D.Bp * 2);
-    if (!last_cta_arrive(counter)) return;
-    double pq = grid_lane_total(part, D.G, 2 * D.Bp, D.Bp, smem);
+    cta_lane_sum((double)dh + (double)dl, D.Bp, s_tmp, s_out);
+    cluster_store(s_out, D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
+    if (!last_cluster_arrive(counter, D.NP)) return;
+    double pq = grid_lane_total(part, D.NP, 2 * D.Bp, D.Bp, s_tmp);
     if ((int)threadIdx.x < D.Bp) {
         SlotScalars& s = sc[threadIdx.x];
         if (s.state == want) {
@@ -253,7 +334,7 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_spmv(Dims D, int want,
             }
         }
     }
-    last_cta_reset(counter);
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // x += alpha p, r -= alpha q (double-float, elementwise)
@@ -271,21 +352,18 @@ __global__ void k_upd(Dims D, int want, float2* __restrict__ x, float2* __restri
     }
 }
 
-// Pre-relaxation from zero and restriction: y1 = omega D^-1 r (r1 = 1) or 0 (r1 = 0),
-// r1 = r - K y1, partial sums of c = Phi^T r1 and of ||r||^2.
-template <int BS, int KP>
-__global__ void __launch_bounds__(POD2G_THREADS) k_pre(Dims D, int want, int PRE,
-    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, const float* __restrict__ vals,
-    const float* __restrict__ dinv, const float2* __restrict__ r, const float* __restrict__ phi,
-    double* part, double* cpart, const SlotScalars* __restrict__ sc) {
-    extern __shared__ float red[];  // [blockDim][kp + 1]
-    __shared__ double smem[POD2G_THREADS];
+// Pre-relaxation from zero and the residual it leaves: y1 = omega D^-1 r (r1 = 1)
+// or 0 (r1 = 0), r1 = r - K y1, written to out (FP32); cluster partial sums of
+// ||r||^2 go to part[cluster][slot].
+template <int BS>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+          const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ r,
+          float* __restrict__ out, double* part, const SlotScalars* __restrict__ sc) {
+    __shared__ double s_tmp[POD2G_THREADS];
+    __shared__ double s_out[POD2G_MAX_BP];
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
-    const int kp = KP, ks = KP + 1;
-    float cacc[KP > 0 ? KP : 1];
-#pragma unroll
-    for (int m = 0; m < (KP > 0 ? KP : 1); ++m) cacc[m] = 0.f;
     float rr = 0.f;
     const float w = (float)D.omega;
     if (on) {
@@ -297,69 +375,120 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_pre(Dims D, int want, int PRE
 #pragma unroll
             for (int a = 0; a < BS; ++a) acc[a] = 0.f;
             if (PRE) {
-                for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
-                    const int j = col_idx[blk];
-                    float yj[BS];
+                float yj[UNROLL][BS], v[UNROLL][BS * BS];
+                row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+                    [&](int u, int blk, int j) {
 #pragma unroll
-                    for (int cc = 0; cc < BS; ++cc) {
-                        const long long o = ((long long)j * BS + cc) * D.Bp + lane;
-                        yj[cc] = w * dinv[o] * r[o].x;
-                    }
-                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+                        for (int cc = 0; cc < BS; ++cc) {
+                            const long long o = ((long long)j * BS + cc) * D.Bp + lane;
+                            yj[u][cc] = w * dinv[o] * r[o].x;
+                        }
+                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                    for (int a = 0; a < BS; ++a)
+                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                    },
+                    [&](int u) {
 #pragma unroll
-                        for (int cc = 0; cc < BS; ++cc) acc[a] = __fmaf_rn(vb[(a * BS + cc) * D.Bp], yj[cc], acc[a]);
-                }
+                        for (int a = 0; a < BS; ++a)
+#pragma unroll
+                            for (int cc = 0; cc < BS; ++cc) acc[a] = __fmaf_rn(v[u][a * BS + cc], yj[u][cc], acc[a]);
+                    });
             }
 #pragma unroll
             for (int a = 0; a < BS; ++a) {
-                const long long d = (long long)i * BS + a;
-                const float2 rv = r[d * D.Bp + lane];
-                const float r1 = rv.x - acc[a];
-                rr = __fmaf_rn(rv.x, rv.x, rr);
-                const float4* ph = reinterpret_cast<const float4*>(phi + d * KP);
-#pragma unroll
-                for (int m4 = 0; m4 < KP / 4; ++m4) {
-                    float4 f = ph[m4];
-                    cacc[4 * m4 + 0] = __fmaf_rn(f.x, r1, cacc[4 * m4 + 0]);
-                    cacc[4 * m4 + 1] = __fmaf_rn(f.y, r1, cacc[4 * m4 + 1]);
-                    cacc[4 * m4 + 2] = __fmaf_rn(f.z, r1, cacc[4 * m4 + 2]);
-                    cacc[4 * m4 + 3] = __fmaf_rn(f.w, r1, cacc[4 * m4 + 3]);
-                }
+                const long long o = ((long long)i * BS + a) * D.Bp + lane;
+                const float rv = r[o].x;
+                out[o] = rv - acc[a];
+                rr = __fmaf_rn(rv, rv, rr);
             }
         }
     }
-    // per-slot CTA sums: ||r||^2 and the kp restriction components
-    cta_lane_sum((double)rr, D.Bp, smem, part + (long long)blockIdx.x * D.Bp * 2);
-    if (KP == 0) return;
+    cta_lane_sum((double)rr, D.Bp, s_tmp, s_out);
+    cluster_store(s_out, D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
+}
+
+// Restriction c = Phi^T r1 for every slot (a tall-skinny product: Phi row-major
+// [n][KP], r1 slot-interleaved [n][Bp]); cluster partial rows cpart[cluster][slot][KP].
+// A thread owns one slot and a strided set of rows; two rows are in flight at once.
+template <int KP>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_restrict(Dims D, int want, long long n, const float* __restrict__ phi, const float* __restrict__ r1,
+           double* cpart, const SlotScalars* __restrict__ sc) {
+    extern __shared__ double s_c[];             // [Bp * KP]
+    __shared__ float red[POD2G_THREADS][9];     // 8 modes at a time (+1: conflict-free rows)
+    const int lane = threadIdx.x & (D.Bp - 1);
+    const bool on = sc[lane].state == want;
+    float cacc[KP];
 #pragma unroll
-    for (int m = 0; m < (KP > 0 ? KP : 1); ++m) red[threadIdx.x * ks + m] = cacc[m];
-    __syncthreads();
-    double* cp = cpart + (long long)blockIdx.x * D.Bp * kp;
-    for (int o = threadIdx.x; o < D.Bp * kp; o += blockDim.x) {
-        const int b = o / kp, m = o - b * kp;
-        double s = 0.0;
-        for (int t = b; t < (int)blockDim.x; t += D.Bp) s += (double)red[t * ks + m];
-        cp[o] = s;
+    for (int m = 0; m < KP; ++m) cacc[m] = 0.f;
+    if (on) {
+        const long long items = n << D.lgBp;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        for (; it + stride < items; it += 2 * stride) {
+            const long long d0 = it >> D.lgBp, d1 = (it + stride) >> D.lgBp;
+            const float x0 = r1[it], x1 = r1[it + stride];
+            const float4* p0 = reinterpret_cast<const float4*>(phi + d0 * KP);
+            const float4* p1 = reinterpret_cast<const float4*>(phi + d1 * KP);
+            float4 f0[KP / 4], f1[KP / 4];
+#pragma unroll
+            for (int m4 = 0; m4 < KP / 4; ++m4) { f0[m4] = __ldg(p0 + m4); f1[m4] = __ldg(p1 + m4); }
+#pragma unroll
+            for (int m4 = 0; m4 < KP / 4; ++m4) {
+                cacc[4 * m4 + 0] = __fmaf_rn(f1[m4].x, x1, __fmaf_rn(f0[m4].x, x0, cacc[4 * m4 + 0]));
+                cacc[4 * m4 + 1] = __fmaf_rn(f1[m4].y, x1, __fmaf_rn(f0[m4].y, x0, cacc[4 * m4 + 1]));
+                cacc[4 * m4 + 2] = __fmaf_rn(f1[m4].z, x1, __fmaf_rn(f0[m4].z, x0, cacc[4 * m4 + 2]));
+                cacc[4 * m4 + 3] = __fmaf_rn(f1[m4].w, x1, __fmaf_rn(f0[m4].w, x0, cacc[4 * m4 + 3]));
+            }
+        }
+        if (it < items) {
+            const long long d0 = it >> D.lgBp;
+            const float x0 = r1[it];
+            const float4* p0 = reinterpret_cast<const float4*>(phi + d0 * KP);
+#pragma unroll
+            for (int m4 = 0; m4 < KP / 4; ++m4) {
+                const float4 f = __ldg(p0 + m4);
+                cacc[4 * m4 + 0] = __fmaf_rn(f.x, x0, cacc[4 * m4 + 0]);
+                cacc[4 * m4 + 1] = __fmaf_rn(f.y, x0, cacc[4 * m4 + 1]);
+                cacc[4 * m4 + 2] = __fmaf_rn(f.z, x0, cacc[4 * m4 + 2]);
+                cacc[4 * m4 + 3] = __fmaf_rn(f.w, x0, cacc[4 * m4 + 3]);
+            }
+        }
     }
+    // per-slot CTA sums of the KP components, 8 at a time
+#pragma unroll
+    for (int m0 = 0; m0 < KP; m0 += 8) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) red[threadIdx.x][u] = cacc[m0 + u];
+        __syncthreads();
+        for (int o = threadIdx.x; o < D.Bp * 8; o += blockDim.x) {
+            const int b = o >> 3, u = o & 7;
+            double s = 0.0;
+            for (int t = b; t < (int)blockDim.x; t += D.Bp) s += (double)red[t][u];
+            s_c[b * KP + m0 + u] = s;
+        }
+    }
+    __syncthreads();
+    cluster_store(s_c, D.Bp * KP, cpart + (long long)(blockIdx.x / CLUSTER) * D.Bp * KP);
 }
 
 // One CTA per slot: convergence test on ||r||^2, coarse right-hand side
-// c = Phi^T r1 (sum over CTAs in order), e_c = L^-T L^-1 c in FP64.
-__global__ void k_coarse(Dims D, int want, int init, const double* __restrict__ part,
-                         const double* __restrict__ cpart, const double* __restrict__ Lc, float* __restrict__ ec,
-                         SlotScalars* sc) {
+// c = Phi^T r1 (sum over partial rows in order), e_c = L^-T L^-1 c in FP64.
+__global__ void k_coarse(Dims D, int want, const double* __restrict__ part, const double* __restrict__ cpart,
+                         const double* __restrict__ Lc, float* __restrict__ ec, SlotScalars* sc) {
     __shared__ double smem[POD2G_THREADS];
     __shared__ double cv[POD2G_MAX_K];
     __shared__ int go;
     const int b = blockIdx.x;
     if (sc[b].state != want) return;
-    // ||r||^2 over CTAs: contiguous ranges per thread, then a fixed tree
+    const int kp = D.kp;
+    const long long nv = (long long)D.Bp * kp;
+    // ||r||^2 over partial rows: contiguous ranges per thread, then a fixed tree
     {
         const int T = blockDim.x;
-        const int g0 = (int)((long long)D.G * threadIdx.x / T), g1 = (int)((long long)D.G * (threadIdx.x + 1) / T);
-        smem[threadIdx.x] = ordered_sum(part + b, g0, g1, (long long)D.Bp * 2);
+        const int g0 = (int)((long long)D.NP * threadIdx.x / T), g1 = (int)((long long)D.NP * (threadIdx.x + 1) / T);
+        smem[threadIdx.x] = ordered_sum(part + b, g0, g1, 2LL * D.Bp);
         __syncthreads();
         for (int h = T / 2; h > 0; h >>= 1) {
             if ((int)threadIdx.x < h) smem[threadIdx.x] += smem[threadIdx.x + h];
@@ -380,13 +509,12 @@ __global__ void k_coarse(Dims D, int want, int init, const double* __restrict__ 
     __syncthreads();
     if (!go || D.k == 0) return;
     // c[m] = sum_g cpart[g][b][m]: thread (m, q) sums a contiguous range of g
-    const int kp = D.kp;
     const int Q = blockDim.x / kp;
     const int m = threadIdx.x % kp, q = threadIdx.x / kp;
     double cs = 0.0;
     if (q < Q) {
-        const int g0 = (int)((long long)D.G * q / Q), g1 = (int)((long long)D.G * (q + 1) / Q);
-        cs = ordered_sum(cpart + (long long)b * kp + m, g0, g1, (long long)D.Bp * kp);
+        const int g0 = (int)((long long)D.NPc * q / Q), g1 = (int)((long long)D.NPc * (q + 1) / Q);
+        cs = ordered_sum(cpart + (long long)b * kp + m, g0, g1, nv);  // rows of the restriction grid
     }
     __syncthreads();
     smem[threadIdx.x] = cs;
@@ -417,47 +545,54 @@ __global__ void k_coarse(Dims D, int want, int init, const double* __restrict__ 
         }
         for (int mm = l; mm < kp; mm += 32) ec[(long long)b * kp + mm] = mm < k ? (float)cv[mm] : 0.f;
     }
-    (void)init;
 }
 
-// y2 = y1 + Phi e_c with y1 = omega D^-1 r (r1 = 1) or 0
-template <int PRE>
-__global__ void k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restrict__ r,
-                       const float* __restrict__ phi, const float* __restrict__ ec, float* __restrict__ y,
-                       const SlotScalars* __restrict__ sc, long long n) {
-    extern __shared__ float s_ec[];  // [Bp][kp + 1] (odd row stride: no bank conflicts across slots)
-    for (int e = threadIdx.x; e < D.Bp * D.kp; e += blockDim.x) s_ec[(e / D.kp) * (D.kp + 1) + e % D.kp] = ec[e];
+// y2 = y1 + Phi e_c with y1 = omega D^-1 r (r1 = 1) or 0; KP a compile-time
+// width so that a row's Phi loads are all issued before they are used.
+template <int PRE, int KP>
+__global__ void __launch_bounds__(POD2G_THREADS)
+k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restrict__ r, const float* __restrict__ phi,
+       const float* __restrict__ ec, float* __restrict__ y, const SlotScalars* __restrict__ sc, long long n) {
+    extern __shared__ float s_ec[];  // [Bp][KP + 1] (odd row stride: no bank conflicts across slots)
+    for (int e = threadIdx.x; e < D.Bp * KP; e += blockDim.x) s_ec[(e / KP) * (KP + 1) + e % KP] = ec[e];
     __syncthreads();
     const int lane = threadIdx.x & (D.Bp - 1);
     if (sc[lane].state != want) return;
     const float w = (float)D.omega;
-    const int kp = D.kp;
-    const float* el = s_ec + lane * (kp + 1);
+    constexpr int KA = KP > 0 ? KP : 4;
+    float e_l[KA];
+#pragma unroll
+    for (int m = 0; m < KP; ++m) e_l[m] = s_ec[lane * (KP + 1) + m];
     const long long items = n << D.lgBp;
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
          it += (long long)gridDim.x * blockDim.x) {
         const long long d = it >> D.lgBp;
+        const float4* ph = reinterpret_cast<const float4*>(phi + d * KP);
+        float4 f[KA / 4];
+#pragma unroll
+        for (int m4 = 0; m4 < KP / 4; ++m4) f[m4] = __ldg(ph + m4);
         float v = PRE ? w * dinv[it] * r[it].x : 0.f;
-        const float4* ph = reinterpret_cast<const float4*>(phi + d * kp);
-        for (int m4 = 0; m4 < kp / 4; ++m4) {
-            float4 f = ph[m4];
-            v = __fmaf_rn(f.x, el[4 * m4 + 0], v);
-            v = __fmaf_rn(f.y, el[4 * m4 + 1], v);
-            v = __fmaf_rn(f.z, el[4 * m4 + 2], v);
-            v = __fmaf_rn(f.w, el[4 * m4 + 3], v);
+        float v2 = 0.f;
+#pragma unroll
+        for (int m4 = 0; m4 < KP / 4; ++m4) {
+            v = __fmaf_rn(f[m4].x, e_l[4 * m4 + 0], v);
+            v2 = __fmaf_rn(f[m4].y, e_l[4 * m4 + 1], v2);
+            v = __fmaf_rn(f[m4].z, e_l[4 * m4 + 2], v);
+            v2 = __fmaf_rn(f[m4].w, e_l[4 * m4 + 3], v2);
         }
-        y[it] = v;
+        y[it] = v + v2;
     }
 }
 
 // s = y2 + omega D^-1 (r - K y2) (r2 = 1) or y2 (r2 = 0); partial r^T s (and
-// r^T s_old for Polak-Ribiere); last CTA: beta, JOINING -> ACTIVE.
+// r^T s_old for Polak-Ribiere); last cluster: beta, JOINING -> ACTIVE.
 template <int BS, int POST>
-__global__ void __launch_bounds__(POD2G_THREADS) k_post(Dims D, int want, int pr,
-    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, const float* __restrict__ vals,
-    const float* __restrict__ dinv, const float2* __restrict__ r, const float* __restrict__ y, float* __restrict__ s,
-    double* part, unsigned* counter, SlotScalars* sc) {
-    __shared__ double smem[POD2G_THREADS];
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+       const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ r,
+       const float* __restrict__ y, float* __restrict__ s, double* part, unsigned* counter, SlotScalars* sc) {
+    __shared__ double s_tmp[POD2G_THREADS];
+    __shared__ double s_out[2 * POD2G_MAX_BP];
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float h = 0.f, l = 0.f, xh = 0.f, xl = 0.f;
@@ -471,17 +606,21 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_post(Dims D, int want, int pr
 #pragma unroll
             for (int a = 0; a < BS; ++a) acc[a] = 0.f;
             if (POST) {
-                for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
-                    const int j = col_idx[blk];
-                    float yj[BS];
+                float yj[UNROLL][BS], v[UNROLL][BS * BS];
+                row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+                    [&](int u, int blk, int j) {
 #pragma unroll
-                    for (int cc = 0; cc < BS; ++cc) yj[cc] = y[((long long)j * BS + cc) * D.Bp + lane];
-                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+                        for (int cc = 0; cc < BS; ++cc) yj[u][cc] = y[((long long)j * BS + cc) * D.Bp + lane];
+                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                    for (int a = 0; a < BS; ++a)
+                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                    },
+                    [&](int u) {
 #pragma unroll
-                        for (int cc = 0; cc < BS; ++cc) acc[a] = __fmaf_rn(vb[(a * BS + cc) * D.Bp], yj[cc], acc[a]);
-                }
+                        for (int a = 0; a < BS; ++a)
+#pragma unroll
+                            for (int cc = 0; cc < BS; ++cc) acc[a] = __fmaf_rn(v[u][a * BS + cc], yj[u][cc], acc[a]);
+                    });
             }
 #pragma unroll
             for (int a = 0; a < BS; ++a) {
@@ -498,12 +637,12 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_post(Dims D, int want, int pr
             }
         }
     }
-    double* pg = part + (long long)blockIdx.x * D.Bp * 2;
-    cta_lane_sum((double)h + (double)l, D.Bp, smem, pg);
-    if (pr) cta_lane_sum((double)xh + (double)xl, D.Bp, smem, pg + D.Bp);
-    if (!last_cta_arrive(counter)) return;
-    double rs = grid_lane_total(part, D.G, 2 * D.Bp, D.Bp, smem);
-    double rsx = pr ? grid_lane_total(part + D.Bp, D.G, 2 * D.Bp, D.Bp, smem) : 0.0;
+    cta_lane_sum((double)h + (double)l, D.Bp, s_tmp, s_out);
+    cta_lane_sum((double)xh + (double)xl, D.Bp, s_tmp, s_out + D.Bp);
+    cluster_store(s_out, 2 * D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
+    if (!last_cluster_arrive(counter, D.NP)) return;
+    double rs = grid_lane_total(part, D.NP, 2 * D.Bp, D.Bp, s_tmp);
+    double rsx = pr ? grid_lane_total(part + D.Bp, D.NP, 2 * D.Bp, D.Bp, s_tmp) : 0.0;
     if ((int)threadIdx.x < D.Bp) {
         SlotScalars& S = sc[threadIdx.x];
         if (S.state == want) {
@@ -518,7 +657,7 @@ __global__ void __launch_bounds__(POD2G_THREADS) k_post(Dims D, int want, int pr
             }
         }
     }
-    last_cta_reset(counter);
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 }  // namespace
@@ -533,8 +672,17 @@ static Dims dims_of(pod2g_ctx* c) {
     D.k = c->k;
     D.kp = c->kp;
     D.G = c->grid_rows;
+    D.NP = c->grid_rows / CLUSTER;
+    D.NPc = batched_grid(c->num_sms, (long long)c->n * c->Bp) / CLUSTER;
     D.omega = c->omega;
     return D;
+}
+
+// grid of the row kernels: a multiple of the cluster size, at most 8 CTAs per SM
+int batched_grid(int num_sms, long long items) {
+    int g = ceil_div(items, POD2G_THREADS);
+    g = std::max(CLUSTER, std::min(g, 8 * num_sms));
+    return ceil_div(g, CLUSTER) * CLUSTER;
 }
 
 #define LAUNCH_BS(KERNEL, ...)                                                         \
@@ -544,22 +692,50 @@ static Dims dims_of(pod2g_ctx* c) {
         else KERNEL<3> __VA_ARGS__;                                                    \
     } while (0)
 
-#define KP_LIST(X, BS) X(BS, 0) X(BS, 8) X(BS, 16) X(BS, 24) X(BS, 32) X(BS, 40) X(BS, 48) X(BS, 64)
-
-template <int BS, int KP>
-static const void* pre_fn() { return (const void*)k_pre<BS, KP>; }
+#define KP_LIST(X) X(8) X(16) X(24) X(32) X(40) X(48) X(64)
 
 template <int BS>
-static void launch_pre(pod2g_ctx* c, Dims D, int want) {
-    dim3 g(D.G), t(POD2G_THREADS);
-    size_t sm = c->smem_pre;
-#define CASE_KP(BS_, KP_)                                                                                  \
-    case KP_:                                                                                              \
-        k_pre<BS_, KP_><<<g, t, sm, c->stream>>>(D, want, c->pre, c->d_row_ptr, c->d_col_idx, c->d_vals32, \
-                                                 c->d_dinv32, c->d_rdf, c->d_phi32, c->d_part, c->d_cpart,  \
-                                                 c->d_sc);                                                 \
+static void launch_smooth1(pod2g_ctx* c, Dims D, int want) {
+    k_smooth1<BS><<<D.G, POD2G_THREADS, 0, c->stream>>>(D, want, c->pre, c->d_row_ptr, c->d_col_idx, c->d_vals32,
+                                                         c->d_dinv32, c->d_rdf, c->d_y32, c->d_part, c->d_sc);
+}
+
+static void launch_restrict(pod2g_ctx* c, Dims D, int want) {
+    const size_t sm = sizeof(double) * c->Bp * c->kp;
+    const int g = D.NPc * CLUSTER;
+#define CASE_KP(KP_)                                                                                           \
+    case KP_:                                                                                                  \
+        k_restrict<KP_><<<g, POD2G_THREADS, sm, c->stream>>>(D, want, c->n, c->d_phi32, c->d_y32, c->d_cpart, \
+                                                             c->d_sc);                                         \
         break;
-    switch (c->kp) { KP_LIST(CASE_KP, BS) }
+    switch (c->kp) { KP_LIST(CASE_KP) }
+#undef CASE_KP
+}
+
+static void launch_prol(pod2g_ctx* c, Dims D, int want) {
+    const size_t sm = sizeof(float) * c->Bp * (c->kp + 1);
+    const long long n = c->n;
+    const int gp = std::max(1, std::min(ceil_div(n * c->Bp, POD2G_THREADS), 8 * c->num_sms));
+#define CASE_KP(KP_)                                                                                              \
+    case KP_:                                                                                                     \
+        if (c->pre)                                                                                               \
+            k_prol<1, KP_><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,    \
+                                                                 c->d_ec, c->d_y32, c->d_sc, n);                  \
+        else                                                                                                      \
+            k_prol<0, KP_><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,    \
+                                                                 c->d_ec, c->d_y32, c->d_sc, n);                  \
+        break;
+    switch (c->kp) {
+        KP_LIST(CASE_KP)
+        case 0:
+            if (c->pre)
+                k_prol<1, 0><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,
+                                                                   c->d_ec, c->d_y32, c->d_sc, n);
+            else
+                k_prol<0, 0><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,
+                                                                   c->d_ec, c->d_y32, c->d_sc, n);
+            break;
+    }
 #undef CASE_KP
 }
 
@@ -583,28 +759,21 @@ static int mark(pod2g_ctx* c) {
     return POD2G_OK;
 }
 
+static int elementwise_grid(pod2g_ctx* c, long long total) {
+    return std::max(1, std::min(ceil_div(total, POD2G_THREADS), 8 * c->num_sms));
+}
+
 // the preconditioner s = AMG(0; K, r, r1, r2) for lanes in state `want`
 static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
-    const long long n = c->n;
-    if (c->bs == 1) launch_pre<1>(c, D, want);
-    else if (c->bs == 2) launch_pre<2>(c, D, want);
-    else launch_pre<3>(c, D, want);
+    LAUNCH_BS(launch_smooth1, (c, D, want));
     P2G_TRY(mark(c));
-    k_coarse<<<c->Bp, POD2G_THREADS, 0, c->stream>>>(D, want, want == SLOT_JOINING, c->d_part, c->d_cpart, c->d_Lc,
-                                                     c->d_ec, c->d_sc);
+    if (c->kp > 0) launch_restrict(c, D, want);
     P2G_TRY(mark(c));
-    size_t sm = sizeof(float) * c->Bp * (c->kp + 1);
-    int gp = std::max(1, std::min(D.G, ceil_div(n * c->Bp, POD2G_THREADS)));
-    if (c->pre)
-        k_prol<1><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32, c->d_ec, c->d_y32,
-                                                        c->d_sc, n);
-    else
-        k_prol<0><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32, c->d_ec, c->d_y32,
-                                                        c->d_sc, n);
+    k_coarse<<<c->Bp, POD2G_THREADS, 0, c->stream>>>(D, want, c->d_part, c->d_cpart, c->d_Lc, c->d_ec, c->d_sc);
     P2G_TRY(mark(c));
-    if (c->bs == 1) launch_post<1>(c, D, want);
-    else if (c->bs == 2) launch_post<2>(c, D, want);
-    else launch_post<3>(c, D, want);
+    launch_prol(c, D, want);
+    P2G_TRY(mark(c));
+    LAUNCH_BS(launch_post, (c, D, want));
     P2G_TRY(mark(c));
     return POD2G_OK;
 }
@@ -612,7 +781,7 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
 // one PCG iteration (Algorithm 3 loop body) for ACTIVE lanes
 static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     const long long total = (long long)c->n * c->Bp;
-    const int ge = std::max(1, std::min(D.G, ceil_div(total, POD2G_THREADS)));
+    const int ge = elementwise_grid(c, total);
     if (c->cap_ev) P2G_CUDA(cudaEventRecordWithFlags(c->cap_ev[c->cap_idx++], c->stream, cudaEventRecordExternal));
     k_p<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_s32, c->d_pdf, c->d_sc, total);
     P2G_TRY(mark(c));
@@ -630,16 +799,25 @@ int batched_alloc(pod2g_ctx* c) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c->num_sms = sms > 0 ? sms : 152;
-    const long long items = (long long)c->nb * c->Bp;
-    c->grid_rows = std::max(1, std::min(ceil_div(items, POD2G_THREADS), 4 * c->num_sms));
-    c->smem_pre = POD2G_THREADS * (c->kp + 1) * (int)sizeof(float);
-    if (c->precision != POD2G_FP64) {
-        const void* f = nullptr;
-#define FN_KP(BS_, KP_) if (c->bs == BS_ && c->kp == KP_) f = pre_fn<BS_, KP_>();
-        KP_LIST(FN_KP, 1) KP_LIST(FN_KP, 2) KP_LIST(FN_KP, 3)
+    c->grid_rows = batched_grid(c->num_sms, (long long)c->nb * c->Bp);
+    if (c->precision != POD2G_FP64 && c->kp > 0) {
+        const int sm_r = c->Bp * c->kp * (int)sizeof(double);
+        const int sm_p = c->Bp * (c->kp + 1) * (int)sizeof(float);
+        const void* fr = nullptr;
+        const void* fp1 = nullptr;
+        const void* fp0 = nullptr;
+#define FN_KP(KP_)                                                      \
+        if (c->kp == KP_) {                                              \
+            fr = (const void*)k_restrict<KP_>;                           \
+            fp1 = (const void*)k_prol<1, KP_>;                           \
+            fp0 = (const void*)k_prol<0, KP_>;                           \
+        }
+        KP_LIST(FN_KP)
 #undef FN_KP
-        if (!f) return POD2G_INVALID_ARG;
-        P2G_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_pre));
+        if (!fr) return POD2G_INVALID_ARG;
+        P2G_CUDA(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_r));
+        P2G_CUDA(cudaFuncSetAttribute(fp1, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
+        P2G_CUDA(cudaFuncSetAttribute(fp0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
     }
     return POD2G_OK;
 }
@@ -668,7 +846,7 @@ int batched_load(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev
     P2G_CUDA(cudaMemcpyAsync(c->d_mask, mask.data(), sizeof(int) * c->Bp, cudaMemcpyHostToDevice, c->stream));
     P2G_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyHostToDevice, c->stream));
     const long long tot = (long long)nslots * c->n;
-    k_load<<<std::max(1, std::min(ceil_div(tot, POD2G_THREADS), 8 * c->num_sms)), POD2G_THREADS, 0, c->stream>>>(
+    k_load<<<elementwise_grid(c, tot), POD2G_THREADS, 0, c->stream>>>(
         b_dev, x0_dev, d_slots, nslots, c->n, c->Bp, c->d_bdf, c->d_xdf, c->d_pdf, c->d_qdf, c->d_s32);
     P2G_TRY(pod2g_check_launch(c));
     LAUNCH_BS(k_resid, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, 0, c->d_mask, c->d_row_ptr, c->d_col_idx,
@@ -684,13 +862,13 @@ static int build_graph(pod2g_ctx* c) {
     Dims D = dims_of(c);
     cudaGraph_t g;
     if (c->timing && c->tev.empty()) {
-        c->tev.resize((size_t)c->chunk * 8);
+        c->tev.resize((size_t)c->chunk * 9);
         for (auto& ev : c->tev) P2G_CUDA(cudaEventCreate(&ev));
     }
     P2G_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int st = POD2G_OK;
     for (int it = 0; it < c->chunk && st == POD2G_OK; ++it) {
-        c->cap_ev = c->timing ? &c->tev[(size_t)it * 8] : nullptr;
+        c->cap_ev = c->timing ? &c->tev[(size_t)it * 9] : nullptr;
         c->cap_idx = 0;
         st = enqueue_iteration(c, D);
     }
@@ -701,7 +879,7 @@ static int build_graph(pod2g_ctx* c) {
     e = cudaGraphInstantiate(&c->graph_exec, g, 0);
     cudaGraphDestroy(g);
     P2G_CUDA(e);
-    c->launches -= (int64_t)7 * c->chunk;  // captured, not launched; counted at each replay
+    c->launches -= (int64_t)8 * c->chunk;  // captured, not launched; counted at each replay
     return POD2G_OK;
 }
 
@@ -710,14 +888,14 @@ static int build_graph(pod2g_ctx* c) {
 int batched_chunk(pod2g_ctx* c) {
     P2G_TRY(build_graph(c));
     P2G_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
-    c->launches += (int64_t)7 * c->chunk;
+    c->launches += (int64_t)8 * c->chunk;
     P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));
     if (c->timing) {
         for (int it = 0; it < c->chunk; ++it)
-            for (int j = 0; j < 7; ++j) {
+            for (int j = 0; j < 8; ++j) {
                 float ms = 0.f;
-                P2G_CUDA(cudaEventElapsedTime(&ms, c->tev[(size_t)it * 8 + j], c->tev[(size_t)it * 8 + j + 1]));
+                P2G_CUDA(cudaEventElapsedTime(&ms, c->tev[(size_t)it * 9 + j], c->tev[(size_t)it * 9 + j + 1]));
                 c->kt_ms[j] += ms;
                 c->kt_n[j] += 1;
             }
@@ -738,7 +916,7 @@ int batched_set_timing(pod2g_ctx* c, int on) {
 }
 
 // Run chunks until every lane in `lanes` is DONE. Bounded: each ACTIVE lane
-// finishes within maxit iterations, so at most max(maxit)/chunk + 1 launches.
+// finishes within maxit iterations, so at most max(maxit)/chunk + 2 launches.
 int batched_run(pod2g_ctx* c, const std::vector<int>& lanes) {
     P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));
@@ -768,8 +946,8 @@ int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, 
                                                               c->d_counters + CNT_RESID, c->d_sc));
     P2G_TRY(pod2g_check_launch(c));
     const long long tot = (long long)nslots * c->n;
-    k_store<<<std::max(1, std::min(ceil_div(tot, POD2G_THREADS), 8 * c->num_sms)), POD2G_THREADS, 0, c->stream>>>(
-        x_dev, d_slots, nslots, c->n, c->Bp, c->d_xdf, c->d_sc);
+    k_store<<<elementwise_grid(c, tot), POD2G_THREADS, 0, c->stream>>>(x_dev, d_slots, nslots, c->n, c->Bp, c->d_xdf,
+                                                                        c->d_sc);
     P2G_TRY(pod2g_check_launch(c));
     P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));

@@ -108,11 +108,10 @@ struct pod2g_ctx {
     double* d_iob = nullptr;            // [B][n] staging of right-hand sides (host-buffer entry points)
     double* d_iox = nullptr;            // [B][n] staging of x0 / x
     int grid_rows = 0;                  // CTAs of the row kernels
-    int smem_pre = 0;                   // dynamic shared memory of the restriction kernel
     cudaGraphExec_t graph_exec = nullptr;
     // per-kernel timing (event-record nodes around each kernel of the captured iterations)
     bool timing = false;
-    std::vector<cudaEvent_t> tev;       // [chunk][8]
+    std::vector<cudaEvent_t> tev;       // [chunk][9]
     cudaEvent_t* cap_ev = nullptr;      // events of the iteration being captured
     int cap_idx = 0;
     double kt_ms[8] = {0};
@@ -258,6 +257,7 @@ int batched_load(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev
 int batched_run(pod2g_ctx* c, const std::vector<int>& lanes);
 int batched_chunk(pod2g_ctx* c);
 int batched_set_timing(pod2g_ctx* c, int on);
+int batched_grid(int num_sms, long long items);
 int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, int* iters, double* relres,
                      int* status);
 int batched_alloc(pod2g_ctx* c);

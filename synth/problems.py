@@ -50,6 +50,9 @@ SPECS = {
     "q4_64": Spec("q4_64", 14, "q4", 64, 8, 20, 60, 7, 2.0 / 3.0, "f32", "mixed", cov=0.3),
     "hex8_8": Spec("hex8_8", 15, "hex8", 8, 12, 10, 30, 3, 0.5, "bf16", "mixed", cov=0.4),
     "hex8_16": Spec("hex8_16", 16, "hex8", 16, 12, 30, 60, 5, 0.5, "bf16", "mixed", cov=0.4),
+    # mid-size case of the 2D elasticity family (profiling: a few GB on the device)
+    "q4_256": Spec("q4_256", 17, "q4", 256, 8, 20, 100, 64, 2.0 / 3.0, "f32", "mixed", cov=0.3),
+    "hex8_32": Spec("hex8_32", 18, "hex8", 32, 12, 30, 100, 32, 0.5, "bf16", "mixed", cov=0.4),
 }
 
 
