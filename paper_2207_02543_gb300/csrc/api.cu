@@ -108,11 +108,12 @@ static void free_all(pod2g_ctx* c) {
                     c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
                     c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
                     c->d_pdf, c->d_qdf, c->d_bdf, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
-                    c->d_mask, c->d_iob, c->d_iox};
+                    c->d_mask, c->d_iob, c->d_iox, c->d_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_scal64) cudaFreeHost(c->h_scal64);
     if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->h_err) cudaFreeHost(c->h_err);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     for (auto ev : c->tev) cudaEventDestroy(ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -228,6 +229,9 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
         ALLOC(c->d_cpart, sizeof(double) * (size_t)Gmax * Bp * std::max(1, kp));
         ALLOC(c->d_sc, sizeof(SlotScalars) * Bp);
         ALLOC(c->d_mask, sizeof(int) * 2 * Bp);
+        ALLOC(c->d_err, sizeof(int));
+        if (cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) { free_all(c); delete c; return POD2G_OOM; }
+        *c->h_err = 0;
         if (cudaMallocHost(&c->h_sc, sizeof(SlotScalars) * Bp) != cudaSuccess) { free_all(c); delete c; return POD2G_OOM; }
         std::memset(c->h_sc, 0, sizeof(SlotScalars) * Bp);
         if (batched_alloc(c) != POD2G_OK) { free_all(c); delete c; return POD2G_INVALID_ARG; }
@@ -259,6 +263,7 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
     }
     if (ok && c->precision != POD2G_FP64) {
         ok = cudaMemset(c->d_sc, 0, sizeof(SlotScalars) * Bp) == cudaSuccess &&
+             cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
              cudaMemset(c->d_vals32, 0, sizeof(float) * tot * Bp) == cudaSuccess &&
              cudaMemset(c->d_dinv32, 0, sizeof(float) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_xdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&

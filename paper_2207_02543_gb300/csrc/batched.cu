@@ -43,7 +43,12 @@
 namespace cg = cooperative_groups;
 
 #define CLUSTER 8   // CTAs per thread-block cluster of the row kernels
-#define UNROLL 3    // blocks of a row fetched ahead
+#ifndef UNROLL
+#define UNROLL 2    // blocks of a row fetched ahead
+#endif
+#ifndef ROW_MINB
+#define ROW_MINB 5  // minimum resident CTAs per SM requested for the sparse row kernels
+#endif
 
 namespace {
 
@@ -189,7 +194,7 @@ __global__ void k_store(double* __restrict__ x, const int* __restrict__ slots, i
 // sets tol2 = tol^2 ||b||^2 (b = 0 or non-finite -> DONE). final: sums
 // ||b - K x||^2 into relres.
 template <int BS>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __restrict__ row_ptr,
         const int32_t* __restrict__ col_idx, const float* __restrict__ vals, const float2* __restrict__ x,
         const float2* __restrict__ b, float2* __restrict__ r, double* part, unsigned* counter, SlotScalars* sc) {
@@ -271,7 +276,7 @@ __global__ void k_p(Dims D, int want, const float* __restrict__ s, float2* __res
 
 // q = K p (double-float), partial p^T q; last cluster: alpha per slot.
 template <int BS>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
        const float* __restrict__ vals, const float2* __restrict__ p, float2* __restrict__ q, double* part,
        unsigned* counter, SlotScalars* sc) {
@@ -356,7 +361,7 @@ __global__ void k_upd(Dims D, int want, float2* __restrict__ x, float2* __restri
 // or 0 (r1 = 0), r1 = r - K y1, written to out (FP32); cluster partial sums of
 // ||r||^2 go to part[cluster][slot].
 template <int BS>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
           const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ r,
           float* __restrict__ out, double* part, const SlotScalars* __restrict__ sc) {
@@ -407,70 +412,89 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
     cluster_store(s_out, D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
 }
 
-// Restriction c = Phi^T r1 for every slot (a tall-skinny product: Phi row-major
-// [n][KP], r1 slot-interleaved [n][Bp]); cluster partial rows cpart[cluster][slot][KP].
-// A thread owns one slot and a strided set of rows; two rows are in flight at once.
-template <int KP>
+// Restriction c = Phi^T r1 for every slot: a tall-skinny product of Phi (row-major
+// [n][KP]) and r1 (slot-interleaved [n][Bp]), register-tiled as an outer product:
+// a thread owns LB consecutive slots x 8 consecutive modes, and per row loads
+// LB values of r1 (one vector load) and 8 of Phi (two float4, shared by the warp)
+// for 8*LB FMAs. A team of (Bp/LB) * (KP/8) threads covers all Bp x KP outputs;
+// the CTA's teams split its contiguous chunk of rows (two rows in flight per
+// thread) and their partials are summed in team order. Cluster partial rows go
+// to cpart[cluster][slot][KP].
+template <int KP, int LB>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
 k_restrict(Dims D, int want, long long n, const float* __restrict__ phi, const float* __restrict__ r1,
            double* cpart, const SlotScalars* __restrict__ sc) {
-    extern __shared__ double s_c[];             // [Bp * KP]
-    __shared__ float red[POD2G_THREADS][9];     // 8 modes at a time (+1: conflict-free rows)
-    const int lane = threadIdx.x & (D.Bp - 1);
-    const bool on = sc[lane].state == want;
-    float cacc[KP];
+    extern __shared__ double s_c[];  // [Bp * KP] doubles, then [teams][Bp * KP] floats
+    const int Bp = D.Bp;
+    const int NOUT = Bp * KP;
+    const int quads = Bp / LB, groups = KP / 8;
+    const int team_size = quads * groups;
+    const int teams = POD2G_THREADS / team_size;
+    const int team = threadIdx.x / team_size, w = threadIdx.x - team * team_size;
+    const int q = w % quads, g = w / quads;
+    const int b0 = q * LB, m0 = g * 8;
+    float* s_team = (float*)(s_c + NOUT);
+    // every slot of the quad is accumulated: outputs of slots that are not in
+    // state `want` are never read (each slot has its own accumulators)
+    const bool on = team < teams;
+    (void)sc;
+    (void)want;
+    float acc[LB][8];
 #pragma unroll
-    for (int m = 0; m < KP; ++m) cacc[m] = 0.f;
+    for (int l = 0; l < LB; ++l)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[l][m] = 0.f;
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long d_begin = blockIdx.x * per, d_end = min(n, d_begin + per);
+    auto load_r = [&](long long d, float* x) {
+        const float* p = r1 + d * Bp + b0;
+        if (LB == 4) { const float4 v = *reinterpret_cast<const float4*>(p); x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+        else if (LB == 8) {
+            const float4 v0 = *reinterpret_cast<const float4*>(p), v1 = *reinterpret_cast<const float4*>(p + 4);
+            x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w; x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+        } else if (LB == 2) { const float2 v = *reinterpret_cast<const float2*>(p); x[0] = v.x; x[1] = v.y; }
+        else x[0] = p[0];
+    };
+    auto fma_row = [&](const float* x, float4 f0, float4 f1) {
+        const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+        for (int l = 0; l < LB; ++l)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[l][m] = __fmaf_rn(f[m], x[l], acc[l][m]);
+    };
     if (on) {
-        const long long items = n << D.lgBp;
-        const long long stride = (long long)gridDim.x * blockDim.x;
-        long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-        for (; it + stride < items; it += 2 * stride) {
-            const long long d0 = it >> D.lgBp, d1 = (it + stride) >> D.lgBp;
-            const float x0 = r1[it], x1 = r1[it + stride];
-            const float4* p0 = reinterpret_cast<const float4*>(phi + d0 * KP);
-            const float4* p1 = reinterpret_cast<const float4*>(phi + d1 * KP);
-            float4 f0[KP / 4], f1[KP / 4];
-#pragma unroll
-            for (int m4 = 0; m4 < KP / 4; ++m4) { f0[m4] = __ldg(p0 + m4); f1[m4] = __ldg(p1 + m4); }
-#pragma unroll
-            for (int m4 = 0; m4 < KP / 4; ++m4) {
-                cacc[4 * m4 + 0] = __fmaf_rn(f1[m4].x, x1, __fmaf_rn(f0[m4].x, x0, cacc[4 * m4 + 0]));
-                cacc[4 * m4 + 1] = __fmaf_rn(f1[m4].y, x1, __fmaf_rn(f0[m4].y, x0, cacc[4 * m4 + 1]));
-                cacc[4 * m4 + 2] = __fmaf_rn(f1[m4].z, x1, __fmaf_rn(f0[m4].z, x0, cacc[4 * m4 + 2]));
-                cacc[4 * m4 + 3] = __fmaf_rn(f1[m4].w, x1, __fmaf_rn(f0[m4].w, x0, cacc[4 * m4 + 3]));
-            }
+        long long d = d_begin + team;
+        for (; d + teams < d_end; d += 2 * teams) {
+            float xa[LB], xb[LB];
+            load_r(d, xa);
+            load_r(d + teams, xb);
+            const float4* pa = reinterpret_cast<const float4*>(phi + d * KP + m0);
+            const float4* pb = reinterpret_cast<const float4*>(phi + (d + teams) * KP + m0);
+            const float4 a0 = __ldg(pa), a1 = __ldg(pa + 1), c0 = __ldg(pb), c1 = __ldg(pb + 1);
+            fma_row(xa, a0, a1);
+            fma_row(xb, c0, c1);
         }
-        if (it < items) {
-            const long long d0 = it >> D.lgBp;
-            const float x0 = r1[it];
-            const float4* p0 = reinterpret_cast<const float4*>(phi + d0 * KP);
-#pragma unroll
-            for (int m4 = 0; m4 < KP / 4; ++m4) {
-                const float4 f = __ldg(p0 + m4);
-                cacc[4 * m4 + 0] = __fmaf_rn(f.x, x0, cacc[4 * m4 + 0]);
-                cacc[4 * m4 + 1] = __fmaf_rn(f.y, x0, cacc[4 * m4 + 1]);
-                cacc[4 * m4 + 2] = __fmaf_rn(f.z, x0, cacc[4 * m4 + 2]);
-                cacc[4 * m4 + 3] = __fmaf_rn(f.w, x0, cacc[4 * m4 + 3]);
-            }
+        if (d < d_end) {
+            float xa[LB];
+            load_r(d, xa);
+            const float4* pa = reinterpret_cast<const float4*>(phi + d * KP + m0);
+            fma_row(xa, __ldg(pa), __ldg(pa + 1));
         }
     }
-    // per-slot CTA sums of the KP components, 8 at a time
+    if (team < teams) {
 #pragma unroll
-    for (int m0 = 0; m0 < KP; m0 += 8) {
-        __syncthreads();
+        for (int l = 0; l < LB; ++l)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) red[threadIdx.x][u] = cacc[m0 + u];
-        __syncthreads();
-        for (int o = threadIdx.x; o < D.Bp * 8; o += blockDim.x) {
-            const int b = o >> 3, u = o & 7;
-            double s = 0.0;
-            for (int t = b; t < (int)blockDim.x; t += D.Bp) s += (double)red[t][u];
-            s_c[b * KP + m0 + u] = s;
-        }
+            for (int m = 0; m < 8; ++m) s_team[team * NOUT + (b0 + l) * KP + m0 + m] = on ? acc[l][m] : 0.f;
     }
     __syncthreads();
-    cluster_store(s_c, D.Bp * KP, cpart + (long long)(blockIdx.x / CLUSTER) * D.Bp * KP);
+    for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < teams; ++t) s += (double)s_team[t * NOUT + o];
+        s_c[o] = s;
+    }
+    __syncthreads();
+    cluster_store(s_c, NOUT, cpart + (long long)(blockIdx.x / CLUSTER) * NOUT);
 }
 
 // One CTA per slot: convergence test on ||r||^2, coarse right-hand side
@@ -587,7 +611,7 @@ k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restric
 // s = y2 + omega D^-1 (r - K y2) (r2 = 1) or y2 (r2 = 0); partial r^T s (and
 // r^T s_old for Polak-Ribiere); last cluster: beta, JOINING -> ACTIVE.
 template <int BS, int POST>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
        const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ r,
        const float* __restrict__ y, float* __restrict__ s, double* part, unsigned* counter, SlotScalars* sc) {
@@ -663,6 +687,8 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
 }  // namespace
 
 // ---------------------------------------------------------------------------- host side
+static int restrict_grid(pod2g_ctx* c);
+
 static Dims dims_of(pod2g_ctx* c) {
     Dims D;
     D.nb = c->nb;
@@ -673,7 +699,7 @@ static Dims dims_of(pod2g_ctx* c) {
     D.kp = c->kp;
     D.G = c->grid_rows;
     D.NP = c->grid_rows / CLUSTER;
-    D.NPc = batched_grid(c->num_sms, (long long)c->n * c->Bp) / CLUSTER;
+    D.NPc = restrict_grid(c) / CLUSTER;
     D.omega = c->omega;
     return D;
 }
@@ -700,16 +726,33 @@ static void launch_smooth1(pod2g_ctx* c, Dims D, int want) {
                                                          c->d_dinv32, c->d_rdf, c->d_y32, c->d_part, c->d_sc);
 }
 
+// slots per thread of the restriction: 4 (vector loads), more when Bp x kp needs it
+static int restrict_lb(int Bp, int kp) {
+    int lb = std::min(4, Bp);
+    while ((Bp / lb) * (kp / 8) > POD2G_THREADS) lb *= 2;
+    return lb;
+}
+static size_t restrict_smem(int Bp, int kp) {
+    if (kp == 0) return 0;
+    const int lb = restrict_lb(Bp, kp);
+    const int teams = POD2G_THREADS / ((Bp / lb) * (kp / 8));
+    return (size_t)Bp * kp * sizeof(double) + (size_t)teams * Bp * kp * sizeof(float);
+}
+static int restrict_grid(pod2g_ctx* c) { return batched_grid(c->num_sms, (long long)2 * c->num_sms * POD2G_THREADS); }
+
+#define LB_LIST(X, KP) X(KP, 1) X(KP, 2) X(KP, 4) X(KP, 8)
 static void launch_restrict(pod2g_ctx* c, Dims D, int want) {
-    const size_t sm = sizeof(double) * c->Bp * c->kp;
+    const size_t sm = restrict_smem(c->Bp, c->kp);
     const int g = D.NPc * CLUSTER;
-#define CASE_KP(KP_)                                                                                           \
-    case KP_:                                                                                                  \
-        k_restrict<KP_><<<g, POD2G_THREADS, sm, c->stream>>>(D, want, c->n, c->d_phi32, c->d_y32, c->d_cpart, \
-                                                             c->d_sc);                                         \
-        break;
-    switch (c->kp) { KP_LIST(CASE_KP) }
+    const int lb = restrict_lb(c->Bp, c->kp);
+#define CASE_LB(KP_, LB_)                                                                                          \
+    if (c->kp == KP_ && lb == LB_)                                                                                 \
+        k_restrict<KP_, LB_><<<g, POD2G_THREADS, sm, c->stream>>>(D, want, c->n, c->d_phi32, c->d_y32, c->d_cpart, \
+                                                                  c->d_sc);
+#define CASE_KP(KP_) LB_LIST(CASE_LB, KP_)
+    KP_LIST(CASE_KP)
 #undef CASE_KP
+#undef CASE_LB
 }
 
 static void launch_prol(pod2g_ctx* c, Dims D, int want) {
@@ -801,19 +844,23 @@ int batched_alloc(pod2g_ctx* c) {
     c->num_sms = sms > 0 ? sms : 152;
     c->grid_rows = batched_grid(c->num_sms, (long long)c->nb * c->Bp);
     if (c->precision != POD2G_FP64 && c->kp > 0) {
-        const int sm_r = c->Bp * c->kp * (int)sizeof(double);
+        const int sm_r = (int)restrict_smem(c->Bp, c->kp);
+        const int lb = restrict_lb(c->Bp, c->kp);
         const int sm_p = c->Bp * (c->kp + 1) * (int)sizeof(float);
         const void* fr = nullptr;
         const void* fp1 = nullptr;
         const void* fp0 = nullptr;
+#define FN_LB(KP_, LB_) \
+        if (c->kp == KP_ && lb == LB_) fr = (const void*)k_restrict<KP_, LB_>;
 #define FN_KP(KP_)                                                      \
+        LB_LIST(FN_LB, KP_)                                              \
         if (c->kp == KP_) {                                              \
-            fr = (const void*)k_restrict<KP_>;                           \
             fp1 = (const void*)k_prol<1, KP_>;                           \
             fp0 = (const void*)k_prol<0, KP_>;                           \
         }
         KP_LIST(FN_KP)
 #undef FN_KP
+#undef FN_LB
         if (!fr) return POD2G_INVALID_ARG;
         P2G_CUDA(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_r));
         P2G_CUDA(cudaFuncSetAttribute(fp1, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
@@ -890,7 +937,9 @@ int batched_chunk(pod2g_ctx* c) {
     P2G_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
     c->launches += (int64_t)8 * c->chunk;
     P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
+    P2G_CUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));
+    if (*c->h_err) return POD2G_TIMEOUT;  // a bounded device wait expired
     if (c->timing) {
         for (int it = 0; it < c->chunk; ++it)
             for (int j = 0; j < 8; ++j) {

@@ -104,6 +104,8 @@ struct pod2g_ctx {
     double* d_cpart = nullptr;          // restriction partials [G][Bp][kp]
     SlotScalars* d_sc = nullptr;        // [Bp]
     SlotScalars* h_sc = nullptr;        // pinned host mirror
+    int* d_err = nullptr;               // device error word: set when a bounded device wait expires
+    int* h_err = nullptr;               // pinned host mirror
     int* d_mask = nullptr;              // [2 Bp] lane mask and slot list for load / finalize
     double* d_iob = nullptr;            // [B][n] staging of right-hand sides (host-buffer entry points)
     double* d_iox = nullptr;            // [B][n] staging of x0 / x
