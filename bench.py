@@ -117,6 +117,15 @@ def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp):
     return {name: per_lane[name] * lane_iters + shared[name] * launches for name in per_lane}
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of these kernels on the
+# workload named (profiles/launches_q4_512_b64.md); valid only for the kernel
+# versions that capture measured.
+NCU_TRAFFIC = {
+    ("q4_512", 64): {"k_spmv": 3162.1e6, "k_smooth1": 3135.3e6, "k_post": 3156.3e6, "k_upd": 1569.0e6,
+                     "k_restrict": 185.4e6, "k_prol": 568.0e6, "k_p": 615.7e6, "k_coarse": 0.8e6},
+}
+
+
 def run_oracle(mode, inst, timeout=900):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -262,7 +271,9 @@ def gb300_arm(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": rates[dom], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": rates[dom] / peaks["hbm_gbs"], "peak_kind": peak_kind,
                 "bytes_per_launch": kb[dom] / max(nl[dom], 1),
-                "ms_per_launch": ktimes[dom][0] / max(nl[dom], 1), "traffic": None,
+                "ms_per_launch": ktimes[dom][0] / max(nl[dom], 1),
+                "traffic": NCU_TRAFFIC.get((args.workload, B), {}).get(dom),
+                "traffic_source": "profiles/launches_q4_512_b64.md" if (args.workload, B) in NCU_TRAFFIC else None,
                 "frac_vs_8TBs": rates[dom] / 8000.0,
                 "all_kernels": {k: {"share": ktimes[k][0] / tot_k, "GBs": round(rates[k], 1),
                                     "ms_per_launch": ktimes[k][0] / max(nl[k], 1)} for k in ktimes},
