@@ -115,7 +115,9 @@ def snapshot_matrix(wl: Workload, count: int | None = None, device: str | None =
         if wl.n > 20_000:
             raise ValueError("large snapshot sets are solved on a CUDA device (device='cuda')")
         return _direct_solve(wl, xis, f)
-    chunk = max(1, min(len(xis), int(6e9 // (wl.problem.nnzb * wl.problem.bs ** 2 * 8 + 64 * wl.n))))
+    # instances per block-diagonal CG batch: values (8 B) + column indices (8 B) + ~8 work vectors
+    budget = float(os.environ.get("POD2G_SNAPSHOT_BYTES", 40e9))
+    chunk = max(1, min(len(xis), int(budget // (wl.problem.nnzb * wl.problem.bs ** 2 * 16 + 64 * wl.n))))
     return _cg_solve_torch(wl, xis, f, device, chunk)
 
 

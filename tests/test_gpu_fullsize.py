@@ -1,0 +1,73 @@
+"""Parity at the benchmark's full size and launch configuration.
+
+2D plane-stress Q4 on a 512 x 512 grid (526,338 unknowns, 2,362,369 blocks), POD basis
+k = 20 from 200 snapshots, 64 instances solved together exactly as bench.py does
+(device-resident FP64 values through pod2g_set_values_batch_dev, pod2g_solve_batch_dev,
+tol 1e-8). Checks:
+  * every instance: status OK, the library's final residual equals an independent
+    FP64 CPU residual ||b - K x|| / ||b|| of the returned x (K from the FP32-rounded
+    values the mixed path solves), and it is <= 1.05e-8;
+  * a sampled instance against the FP64 oracle run on the same rounded values and
+    rounded basis: relative 2-norm error of x <= 1e-6 and iteration counts within +-2.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+from oracle import pod2g_oracle as O  # noqa: E402
+from synth.problems import Workload  # noqa: E402
+from synth.rounding import round_f32, round_phi  # noqa: E402
+from synth.snapshots import pod_basis  # noqa: E402
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2207_02543_gb300 as p
+    return p
+
+
+def _run_batch(pkg, name, sample):
+    wl = Workload(name)
+    P = wl.problem
+    B = wl.spec.batch
+    Phi = pod_basis(wl, device="cuda")
+    prec = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
+    xis = wl.query_thetas(B)
+    vals = wl.values_torch(xis, device="cuda").reshape(B, -1).contiguous()
+    b = torch.from_numpy(wl.rhs(B)).cuda()
+    x = torch.empty_like(b)
+    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=prec, omega=wl.spec.omega, max_batch=B)
+    slots = list(range(B))
+    st, sts = s.set_values_batch_dev(slots, vals)
+    assert st == pkg.OK
+    iters, rel, status, rc = s.solve_batch_dev(slots, b, x, tol=TOL, maxit=5000)
+    s.close()
+    assert rc == pkg.OK and np.all(status == 0)
+    X = x.cpu().numpy()
+    bh = b.cpu().numpy()
+    for i in range(B):
+        v = round_f32(vals[i].cpu().numpy())
+        K = P.csr(v)
+        true_rel = np.linalg.norm(bh[i] - K @ X[i]) / np.linalg.norm(bh[i])
+        assert true_rel <= 1.05 * TOL, (i, true_rel)
+        assert abs(true_rel - rel[i]) <= 1e-3 * TOL + 1e-12, (i, true_rel, rel[i])
+    phi_used = round_phi(Phi, wl.spec.phi_dtype)
+    for i in sample:
+        K = P.csr(round_f32(vals[i].cpu().numpy()))
+        ref = O.pod2g_pcg(K, bh[i], None, phi_used, wl.spec.omega, TOL, 5000)
+        assert ref.status == O.OK
+        err = np.linalg.norm(X[i] - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-6, (i, err)
+        assert abs(int(iters[i]) - ref.iters) <= 2, (i, iters[i], ref.iters)
+
+
+def test_q4_512_batch64_full_size(pkg):
+    _run_batch(pkg, "q4_512", sample=[37])
