@@ -102,6 +102,11 @@ def _cg_solve_torch(wl: Workload, xis: np.ndarray, f: np.ndarray, device: str, c
             beta = torch.where(active > 0, rz_new / rz, torch.zeros_like(rz))
             p = z + (beta[:, None] * p.view(c, n)).view(-1)
             rz = rz_new
+        # verify every snapshot with an independent residual (row-by-row products, no batching)
+        res = b - (A @ x.unsqueeze(1)).squeeze(1)
+        rel = torch.linalg.vector_norm(res.view(c, n), dim=1) / bnorm
+        if float(rel.max()) > 100 * tol:
+            raise RuntimeError(f"snapshot solve did not converge: max relative residual {float(rel.max()):.3e}")
         U[:, s:s + c] = x.view(c, n).T.cpu().numpy()
         del A, vals
     return U
@@ -117,7 +122,8 @@ def snapshot_matrix(wl: Workload, count: int | None = None, device: str | None =
         return _direct_solve(wl, xis, f)
     # instances per block-diagonal CG batch: values (8 B) + column indices (8 B) + ~8 work vectors
     budget = float(os.environ.get("POD2G_SNAPSHOT_BYTES", 40e9))
-    chunk = max(1, min(len(xis), int(budget // (wl.problem.nnzb * wl.problem.bs ** 2 * 16 + 64 * wl.n))))
+    nnz = wl.problem.nnzb * wl.problem.bs ** 2
+    chunk = max(1, min(len(xis), int(budget // (nnz * 16 + 64 * wl.n)), (2 ** 30) // nnz))  # well inside int32 limits
     return _cg_solve_torch(wl, xis, f, device, chunk)
 
 

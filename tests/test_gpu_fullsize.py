@@ -54,15 +54,17 @@ def _run_batch(pkg, name, sample):
     X = x.cpu().numpy()
     bh = b.cpu().numpy()
     for i in range(B):
-        v = round_f32(vals[i].cpu().numpy())
+        v = round_f32(vals[i].cpu().numpy()).reshape(-1, P.bs, P.bs)
         K = P.csr(v)
         true_rel = np.linalg.norm(bh[i] - K @ X[i]) / np.linalg.norm(bh[i])
         assert true_rel <= 1.05 * TOL, (i, true_rel)
         assert abs(true_rel - rel[i]) <= 1e-3 * TOL + 1e-12, (i, true_rel, rel[i])
     phi_used = round_phi(Phi, wl.spec.phi_dtype)
     for i in sample:
-        K = P.csr(round_f32(vals[i].cpu().numpy()))
+        K = P.csr(round_f32(vals[i].cpu().numpy()).reshape(-1, P.bs, P.bs))
         ref = O.pod2g_pcg(K, bh[i], None, phi_used, wl.spec.omega, TOL, 5000)
+        print(f"instance {i}: gpu iters {iters[i]} oracle iters {ref.iters}; oracle history tail "
+              f"{[f'{h:.3e}' for h in ref.history[-40:]]}")
         assert ref.status == O.OK
         err = np.linalg.norm(X[i] - ref.x) / np.linalg.norm(ref.x)
         assert err <= 1e-6, (i, err)
