@@ -102,12 +102,13 @@ def _cg_solve_torch(wl: Workload, xis: np.ndarray, f: np.ndarray, device: str, c
             beta = torch.where(active > 0, rz_new / rz, torch.zeros_like(rz))
             p = z + (beta[:, None] * p.view(c, n)).view(-1)
             rz = rz_new
-        # verify every snapshot with an independent residual (row-by-row products, no batching)
-        res = b - (A @ x.unsqueeze(1)).squeeze(1)
-        rel = torch.linalg.vector_norm(res.view(c, n), dim=1) / bnorm
-        if float(rel.max()) > 100 * tol:
-            raise RuntimeError(f"snapshot solve did not converge: max relative residual {float(rel.max()):.3e}")
         U[:, s:s + c] = x.view(c, n).T.cpu().numpy()
+        # check the first and last snapshot of the batch with scipy's SpMV (independent of cuSPARSE)
+        for t in sorted({0, c - 1}):
+            K = P.csr(wl.values(part[t]))
+            rel = np.linalg.norm(f - K @ U[:, s + t]) / np.linalg.norm(f)
+            if not rel <= 100 * tol:
+                raise RuntimeError(f"snapshot solve did not converge: relative residual {rel:.3e}")
         del A, vals
     return U
 
