@@ -56,9 +56,14 @@ def _run_batch(pkg, name, sample):
     for i in range(B):
         v = round_f32(vals[i].cpu().numpy()).reshape(-1, P.bs, P.bs)
         K = P.csr(v)
-        true_rel = np.linalg.norm(bh[i] - K @ X[i]) / np.linalg.norm(bh[i])
-        assert true_rel <= 1.05 * TOL, (i, true_rel)
-        assert abs(true_rel - rel[i]) <= 1e-3 * TOL + 1e-12, (i, true_rel, rel[i])
+        bn = np.linalg.norm(bh[i])
+        true_rel = np.linalg.norm(bh[i] - K @ X[i]) / bn
+        # rounding-error bound of a computed residual b - K x: each row's terms |K_ij x_j| and
+        # |b_i| carry a relative error of at most ~u, u = 2^-47 for double-float (2^-53 FP64)
+        scale = np.linalg.norm(abs(K) @ np.abs(X[i]) + np.abs(bh[i])) / bn
+        bound = 32 * 2.0 ** -47 * scale
+        assert true_rel <= 1.05 * TOL + bound, (i, true_rel, bound)
+        assert abs(true_rel - rel[i]) <= bound + 1e-3 * true_rel, (i, true_rel, rel[i], bound)
     phi_used = round_phi(Phi, wl.spec.phi_dtype)
     for i in sample:
         K = P.csr(round_f32(vals[i].cpu().numpy()).reshape(-1, P.bs, P.bs))
@@ -73,3 +78,10 @@ def _run_batch(pkg, name, sample):
 
 def test_q4_512_batch64_full_size(pkg):
     _run_batch(pkg, "q4_512", sample=[37])
+
+
+@pytest.mark.skipif(not __import__("os").environ.get("POD2G_FULLSIZE_3D"),
+                    reason="about 15 minutes (300 3D snapshot solves); set POD2G_FULLSIZE_3D=1")
+def test_hex8_64_batch32_full_size(pkg):
+    # 3D Hex8 elasticity 64^3 (823,875 unknowns, 3x3 BSR), k = 30 from 300 snapshots, BF16 basis, 32 instances
+    _run_batch(pkg, "hex8_64", sample=[5])
