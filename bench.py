@@ -188,6 +188,27 @@ def reference_arm(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- replicas
+def replica_offset(rank: int, batch: int) -> int:
+    """First query index of a replica: rank r solves instances [r*batch, (r+1)*batch) (no overlap)."""
+    return rank * batch
+
+
+def max_over_ranks(ms: float, dist=None, device="cuda") -> float:
+    """Step time of the whole job: the slowest rank's (a MAX all-reduce; identity on one rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms_max: float, world: int, batch: int) -> float:
+    """Whole-job solves/s: every rank solves `batch` instances per step."""
+    return world * batch / (ms_max / 1e3)
+
+
 # ----------------------------------------------------------------------------- GB300 arm
 def gb300_arm(args):
     import numpy as np
@@ -211,9 +232,9 @@ def gb300_arm(args):
     Phi = pod_basis(wl, device="cuda")
     t_phi = time.time() - t0
     # instances of this replica: distinct per rank
-    xis = wl.query_thetas(B, offset=rank * B)
+    xis = wl.query_thetas(B, offset=replica_offset(rank, B))
     vals = wl.values_torch(xis, device="cuda").reshape(B, -1).contiguous()      # FP64, resident in HBM
-    b_dev = torch.from_numpy(wl.rhs(B, offset=rank * B)).cuda()
+    b_dev = torch.from_numpy(wl.rhs(B, offset=replica_offset(rank, B))).cuda()
     x_dev = torch.empty_like(b_dev)
     stream = torch.cuda.Stream()
     s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.MIXED_FP32PHI, omega=wl.spec.omega,
@@ -252,11 +273,8 @@ def gb300_arm(args):
     launches = s.launch_count() - l0
     ktimes = s.kernel_times()
     s.kernel_timing(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * B / (ms / 1e3)
+    ms = max_over_ranks(ms, dist)
+    value = job_value(ms, world, B)
 
     # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
     peaks, peak_kind = measured_peaks()

@@ -163,6 +163,11 @@ int pod2g_info(pod2g_t ctx, int* n, int* nnzb, int* k, int* max_batch);
 /* Number of kernel launches the context has issued (for launch accounting). */
 int64_t pod2g_launch_count(pod2g_t ctx);
 
+/* Device memory held by the context, in bytes (what pod2g_create allocated and
+ * checked against hbm_budget); 0 for NULL. Serving front ends use it to admit
+ * further problems under a shared HBM budget. */
+int64_t pod2g_device_bytes(pod2g_t ctx);
+
 /* Per-kernel timing of the batched PCG iteration (mixed contexts only). With
  * on != 0, CUDA events are recorded around each of the 8 kernels of every
  * iteration inside the CUDA graph, and accumulated after each graph launch;

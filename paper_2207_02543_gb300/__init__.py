@@ -22,7 +22,7 @@ EXPORTS = [
     "pod2g_default_opts", "pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
     "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
     "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_kernel_timing", "pod2g_kernel_times",
-    "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc",
+    "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc", "pod2g_device_bytes",
 ]
 NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
 TOO_LARGE = 11
@@ -69,6 +69,8 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_info.argtypes = [P, IP, IP, IP, IP]
     lib.pod2g_launch_count.argtypes = [P]
     lib.pod2g_launch_count.restype = C.c_int64
+    lib.pod2g_device_bytes.argtypes = [P]
+    lib.pod2g_device_bytes.restype = C.c_int64
     lib.pod2g_kernel_timing.argtypes = [P, I]
     lib.pod2g_kernel_times.argtypes = [P, DP, C.POINTER(C.c_int64)]
     lib.pod2g_kernel_timing.restype = C.c_int
@@ -154,6 +156,9 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(self._lib.pod2g_launch_count(self.h))
+
+    def device_bytes(self) -> int:
+        return int(self._lib.pod2g_device_bytes(self.h))
 
     def kernel_timing(self, on: bool = True) -> int:
         return self._lib.pod2g_kernel_timing(self.h, int(on))
@@ -276,3 +281,48 @@ def solve_noalloc(row_ptr_dev, col_idx_dev, bs, values_dev, phi_dev, k, b_dev, x
                                  ptr(phi_dev), k, C.byref(o), ptr(b_dev), ptr(x0_dev), tol, maxit, ptr(x_dev),
                                  C.byref(it), C.byref(rr), C.byref(st), C.c_void_p(stream) if stream else None)
     return rc, it.value, rr.value, st.value
+
+
+class ServingMix:
+    """Requests for several registered problems, served concurrently.
+
+    Each problem gets its own context (its pattern, POD basis and instance slots) whose
+    serving worker batches that problem's requests continuously; the contexts run on
+    their own streams, so the problems' work overlaps on the device. Problems are
+    admitted under one HBM budget: registering a problem whose context would exceed
+    the remaining budget fails with ADMISSION. Requests beyond a problem's queue
+    limit are refused with ADMISSION by pod2g_submit."""
+
+    def __init__(self, hbm_budget: int, max_queue: int = 1024):
+        self.budget = int(hbm_budget)
+        self.max_queue = max_queue
+        self.solvers = {}
+
+    def used_bytes(self) -> int:
+        return sum(s.device_bytes() for s in self.solvers.values())
+
+    def register(self, name, row_ptr, col_idx, bs, phi, **kw) -> int:
+        remaining = self.budget - self.used_bytes()
+        if remaining <= 0:
+            return ADMISSION
+        try:
+            s = Solver(row_ptr, col_idx, bs, phi, hbm_budget=remaining, **kw)
+        except Pod2gError as e:
+            return e.status
+        s.serve_start(self.max_queue)
+        self.solvers[name] = s
+        return OK
+
+    def submit(self, name, values, b, x0=None, tol=1e-8, maxit=1000):
+        st, t = self.solvers[name].submit(values, b, x0=x0, tol=tol, maxit=maxit)
+        return st, (name, t)
+
+    def poll(self, handle):
+        name, t = handle
+        return self.solvers[name].poll(t)
+
+    def close(self):
+        for s in self.solvers.values():
+            s.serve_stop()
+            s.close()
+        self.solvers = {}

@@ -295,6 +295,8 @@ int pod2g_info(pod2g_t c, int* n, int* nnzb, int* k, int* max_batch) {
 
 int64_t pod2g_launch_count(pod2g_t c) { return c ? (int64_t)c->launches : 0; }
 
+int64_t pod2g_device_bytes(pod2g_t c) { return c ? (int64_t)c->allocated : 0; }
+
 int pod2g_kernel_timing(pod2g_t c, int on) {
     if (!c || c->serving) return POD2G_INVALID_ARG;
     return batched_set_timing(c, on);
