@@ -277,3 +277,38 @@ def spectral_radius_estimate(K, Dinv, steps=30, seed=0) -> float:
         lam = float(np.linalg.norm(w))
         v = w / lam
     return lam
+
+
+# ----------------------------------------------------------------------------- Algorithm 2 as a solver
+def pod2g_stationary(K, f, u0, Phi, omega, tol, maxit, r1=1, r2=1) -> PCGResult:
+    """POD-2G used directly as the iterative solver (Algorithm 2, Section 3.3): repeat
+    the two-grid cycle on the current approximation while ||f - K u|| > tol ||f||
+    (the guard of Algorithm 2 read as ">"), at most maxit cycles. iters = cycles applied."""
+    f = np.asarray(f, dtype=np.float64)
+    n = f.shape[0]
+    fnorm = float(np.linalg.norm(f))
+    if fnorm == 0.0:
+        return PCGResult(np.zeros(n), 0, OK, 0.0, [0.0])
+    try:
+        st = pod2g_setup(K, Phi, omega, r1, r2)
+    except np.linalg.LinAlgError:
+        return PCGResult(np.zeros(n) if u0 is None else np.array(u0, float), 0, NOT_SPD, np.nan)
+    u = np.zeros(n) if u0 is None else np.array(u0, dtype=np.float64)
+    r = f - K @ u
+    hist = [float(np.linalg.norm(r)) / fnorm]
+    k = 0
+    status = NOT_CONVERGED
+    while True:
+        if np.linalg.norm(r) <= tol * fnorm:
+            status = OK
+            break
+        if k >= maxit:
+            break
+        u = two_grid_cycle(K, f, u, st.Phi, st.L_c, st.Dinv, omega, r1, r2)
+        r = f - K @ u
+        k += 1
+        hist.append(float(np.linalg.norm(r)) / fnorm)
+        if not np.isfinite(hist[-1]):
+            status = BREAKDOWN
+            break
+    return PCGResult(u, k, status, hist[-1], hist)

@@ -313,3 +313,47 @@ def test_planted_beta_mistake_is_caught(monkeypatch):
     assert np.linalg.norm(x - xb) > 1e-6 * np.linalg.norm(xb)
     good = O.pcg(K, f, None, app, 1e-30, 3)
     assert np.linalg.norm(good.x - xb) <= 1e-9 * np.linalg.norm(xb)
+
+
+# ----------------------------------------------------------------------------- Algorithm 2 as a solver
+def test_stationary_iterates_follow_error_operator_powers():
+    P, K = _small_system(15, ne=6)
+    Phi = _basis(K, 4)
+    n = K.shape[0]
+    st = O.pod2g_setup(K, Phi, 2 / 3)
+    E = O.two_grid_error_operator(K, Phi, st.Dinv, 2 / 3)
+    rng = np.random.default_rng(8)
+    f = rng.standard_normal(n)
+    u0 = rng.standard_normal(n)
+    xs = np.linalg.solve(K.toarray(), f)
+    for k in (1, 3, 7):
+        res = O.pod2g_stationary(K, f, u0, Phi, 2 / 3, 0.0, k)
+        assert res.iters == k
+        assert np.allclose(xs - res.x, np.linalg.matrix_power(E, k) @ (xs - u0), atol=1e-10 * np.abs(xs).max())
+
+
+def test_stationary_converges_with_contraction_rate():
+    P, K = _small_system(16, ne=10)
+    Phi = _basis(K, 6)
+    st = O.pod2g_setup(K, Phi, 2 / 3)
+    E = O.two_grid_error_operator(K, Phi, st.Dinv, 2 / 3)
+    rho = max(abs(np.linalg.eigvals(E)))
+    assert rho < 1
+    res = O.pod2g_stationary(K, P.f0, None, Phi, 2 / 3, 1e-8, 5000)
+    assert res.status == O.OK and res.relres <= 1e-8
+    # the residual contracts asymptotically at about rho per cycle
+    h = np.array(res.history)
+    tail = (h[-1] / h[-11]) ** 0.1
+    assert tail <= rho * 1.05
+    xs = np.linalg.solve(K.toarray(), P.f0)
+    assert np.linalg.norm(res.x - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+def test_stationary_special_inputs():
+    P, K = _small_system(17)
+    Phi = _basis(K, 3)
+    n = K.shape[0]
+    r = O.pod2g_stationary(K, np.zeros(n), np.ones(n), Phi, 2 / 3, 1e-8, 10)
+    assert r.iters == 0 and np.all(r.x == 0)
+    r = O.pod2g_stationary(K, P.f0, None, Phi, 2 / 3, 1e-14, 3)
+    assert r.iters == 3 and r.status == O.NOT_CONVERGED
