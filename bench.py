@@ -126,15 +126,32 @@ NCU_TRAFFIC = {
 }
 
 
-def run_oracle(mode, inst, timeout=900):
+def run_oracle(mode, inst, timeout=900, workload=WORKLOAD, tol=TOL, method="pcg"):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    r = subprocess.run([sys.executable, "-m", "oracle.timing", WORKLOAD, str(inst), str(mode), str(TOL)],
+    r = subprocess.run([sys.executable, "-m", "oracle.timing", workload, str(inst), str(mode), str(tol), method],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def fmt_tol(tol: float) -> str:
+    return f"{tol:.0e}".replace("e-0", "e-")
+
+
+def method_name(method: str) -> str:
+    return "POD-2G-PCG" if method == "pcg" else "POD-2G stationary"
+
+
+def workload_desc(wl, batch: int, tol: float) -> str:
+    sp, P = wl.spec, wl.problem
+    kind = {"q1": f"2D Poisson Q1 {sp.ne}x{sp.ne}, lognormal kappa",
+            "q4": f"2D plane-stress Q4 {sp.ne}x{sp.ne}, lognormal E (CoV {sp.cov})",
+            "hex8": f"3D elasticity Hex8 {sp.ne}^3, lognormal E (CoV {sp.cov})"}[sp.kind]
+    return (f"{kind}: {P.n:,} dofs, {P.bs}x{P.bs} BSR, {sp.m}-term KL, k={sp.k} POD from {sp.n_snap} snapshots "
+            f"({sp.phi_dtype} Phi), batch {batch}, tol {fmt_tol(tol)}")
 
 
 # ----------------------------------------------------------------------------- reference arm (oracle)
@@ -237,14 +254,17 @@ def gb300_arm(args):
     b_dev = torch.from_numpy(wl.rhs(B, offset=replica_offset(rank, B))).cuda()
     x_dev = torch.empty_like(b_dev)
     stream = torch.cuda.Stream()
-    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.MIXED_FP32PHI, omega=wl.spec.omega,
-                   max_batch=B, stream=stream.cuda_stream)
+    precision = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
+    method = pkg.STATIONARY if args.method == "stationary" else pkg.PCG
+    tol, maxit = args.tol, args.maxit
+    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=precision, omega=wl.spec.omega,
+                   max_batch=B, stream=stream.cuda_stream, method=method)
     slots = list(range(B))
 
     def step():
         st, sts = s.set_values_batch_dev(slots, vals)
         assert st == pkg.OK, pkg.strerror(st)
-        iters, rel, status, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=TOL, maxit=MAXIT)
+        iters, rel, status, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=tol, maxit=maxit)
         assert rc == pkg.OK, (pkg.strerror(rc), status)
         return iters, rel
 
@@ -309,21 +329,22 @@ def gb300_arm(args):
         for _ in range(e2e_steps):
             for i in slots:
                 assert s.set_values(i, vals_h[i]) == pkg.OK
-            X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=TOL, maxit=MAXIT)
+            X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=tol, maxit=maxit)
             assert rc == pkg.OK
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         extra["e2e"] = {"value": B / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(vals_h.nbytes + b_h.nbytes),
                         "d2h_bytes_per_step": int(X.nbytes)}
         # plain FP64 one-at-a-time baseline on the same GPU
         if not args.no_plain:
-            sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1)
+            sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1,
+                            method=method)
             nplain = 2
             times, its = [], []
             for i in range(nplain):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 assert sp.set_values(0, vals[i]) == pkg.OK
-                xp, itp, relp, stp = sp.solve(0, b_h[i], tol=TOL, maxit=MAXIT)
+                xp, itp, relp, stp = sp.solve(0, b_h[i], tol=tol, maxit=maxit)
                 torch.cuda.synchronize()
                 times.append(time.perf_counter() - t0)
                 its.append(itp)
@@ -333,28 +354,30 @@ def gb300_arm(args):
                                    "iters": its, "ratio_batched_over_plain": value / (1.0 / statistics.mean(times))}
         # serving: Poisson arrivals at ~70% of the batched throughput, continuous batching
         if not args.no_serve:
-            extra["serving"] = serve_latency(s, pkg, wl, vals_h, b_h, rate=0.7 * value, nreq=args.serve_requests)
+            extra["serving"] = serve_latency(s, pkg, wl, vals_h, b_h, rate=0.7 * value, nreq=args.serve_requests,
+                                             tol=tol, maxit=maxit)
         # CPU baseline: the oracle on a bounded sample (single thread)
         if not args.no_cpu:
             try:
-                o = run_oracle(100, 0)
+                o = run_oracle(100, 0, workload=args.workload, tol=tol, method=args.method)
                 it_full = int(iters[0])
                 cpu_val = 1.0 / (o["seconds_per_iteration"] * it_full)
                 extra["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                         "sample": f"instance 0, first 100 POD-2G-PCG iterations of the FP64 oracle "
-                                                   f"(one thread), scaled by the instance's iteration count {it_full}"}
+                                         "sample": f"instance 0, first 100 {method_name(args.method)} iterations of "
+                                                   f"the FP64 oracle (one thread), scaled by the instance's "
+                                                   f"iteration count {it_full}"}
             except Exception as e:  # noqa: BLE001
                 extra["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                          "sample": f"failed: {e}"[:200]}
     s.close()
     if rank == 0:
         line = {
-            "metric": "solves/s at rel. residual 1e-8 (batched POD-2G-PCG)", "value": value, "unit": "solves/s",
+            "metric": f"solves/s at rel. residual {fmt_tol(tol)} (batched {method_name(args.method)})",
+            "value": value, "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
-            "config": {"workload": "2D plane-stress Q4 512x512 (526,338 dofs, 2x2 BSR), lognormal E (8-term KL, "
-                                   "CoV 0.3), k=20 POD from 200 snapshots, batch 64, tol 1e-8",
+            "config": {"workload": workload_desc(wl, B, tol), "method": method_name(args.method),
                        "batch": B, "n": P.n, "nnzb": P.nnzb, "k": wl.spec.k, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (4.8 GB FP64 values per step)",
                        "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
@@ -371,7 +394,7 @@ def gb300_arm(args):
     return 0
 
 
-def serve_latency(s, pkg, wl, vals_h, b_h, rate, nreq):
+def serve_latency(s, pkg, wl, vals_h, b_h, rate, nreq, tol=TOL, maxit=MAXIT):
     import numpy as np
     rng = np.random.default_rng(3000)
     gaps = rng.exponential(1.0 / rate, nreq)
@@ -383,7 +406,7 @@ def serve_latency(s, pkg, wl, vals_h, b_h, rate, nreq):
         t_next += gaps[i]
         while time.perf_counter() < t_next:
             time.sleep(0.0002)
-        st, t = s.submit(vals_h[i % len(vals_h)], b_h[i % len(b_h)], tol=TOL, maxit=MAXIT)
+        st, t = s.submit(vals_h[i % len(vals_h)], b_h[i % len(b_h)], tol=tol, maxit=maxit)
         assert st == pkg.OK
         tickets.append(t)
     lat = []
@@ -415,6 +438,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling of smaller cases)")
     ap.add_argument("--batch", type=int, default=0, help="instances per step (default: the workload's batch)")
+    ap.add_argument("--method", default="pcg", choices=["pcg", "stationary"],
+                    help="pcg: Algorithm 3; stationary: the two-grid cycle of Algorithm 2 iterated on its own")
+    ap.add_argument("--tol", type=float, default=TOL)
+    ap.add_argument("--maxit", type=int, default=MAXIT)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -74,6 +74,11 @@ extern "C" {
 #define POD2G_MIXED_FP32PHI  1
 #define POD2G_MIXED_BF16PHI  2
 
+/* solution methods */
+#define POD2G_PCG            0  /* PCG preconditioned by one POD-2G cycle from zero (Algorithm 3) */
+#define POD2G_STATIONARY     1  /* the POD-2G two-grid cycle itself as the iteration (Algorithm 2,
+                                   Section 3.3): u <- u + AMG(0; K, f - K u, r1, r2) */
+
 typedef struct pod2g_ctx* pod2g_t;
 
 /* Shared sparsity pattern (host arrays, copied by pod2g_create). */
@@ -96,6 +101,7 @@ typedef struct {
     int64_t spin_limit;       /* bound on host polling iterations of a solve (0 = default) */
     int chunk;                /* PCG iterations per CUDA-graph launch in the batched path (even, default 8) */
     void* stream;             /* cudaStream_t to run on; NULL = a stream owned by the context */
+    int method;               /* POD2G_PCG (default) or POD2G_STATIONARY; iters then counts cycles */
 } pod2g_opts;
 
 /* Fill *opts with defaults. Never fails. */
@@ -198,7 +204,7 @@ void pod2g_destroy(pod2g_t ctx);
  * (nnzb*bs*bs doubles, row-major blocks), phi_dev (n*k doubles, column-major, may
  * be NULL when k = 0), b_dev and x0_dev (n doubles; x0_dev NULL = zero). opts:
  * omega, pre, post, beta_pr are used (NULL = defaults); precision, max_batch,
- * hbm_budget, chunk and stream are ignored. Output: x_dev (n doubles, device);
+ * hbm_budget, chunk, stream and method are ignored (the method is always PCG). Output: x_dev (n doubles, device);
  * iters, relres, status (host, may be NULL) as for pod2g_solve. stream: the
  * cudaStream_t to run on (NULL = the legacy default stream).
  *

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE: started by bench.py in fresh single-threaded processes
 (BLAS threads pinned to 1), never by the solver library.
 
-    python -m oracle.timing <workload> <instance> <iterations|full> <tol>
+    python -m oracle.timing <workload> <instance> <iterations|full> <tol> [pcg|stationary]
 
 prints one JSON object: seconds, iterations run, seconds per iteration, and for
 a full solve the iteration count and the true relative residual.
@@ -18,6 +18,7 @@ import time
 
 def main(argv):
     name, inst, mode, tol = argv[0], int(argv[1]), argv[2], float(argv[3])
+    method = argv[4] if len(argv) > 4 else "pcg"
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)
@@ -37,7 +38,8 @@ def main(argv):
     b = wl.rhs(inst + 1)[inst]
     maxit = 100000 if mode == "full" else int(mode)
     t0 = time.perf_counter()
-    res = O.pod2g_pcg(K, b, None, phi, wl.spec.omega, tol if mode == "full" else 0.0, maxit)
+    solve = O.pod2g_pcg if method == "pcg" else O.pod2g_stationary
+    res = solve(K, b, None, phi, wl.spec.omega, tol if mode == "full" else 0.0, maxit)
     dt = time.perf_counter() - t0
     out = dict(workload=name, instance=inst, seconds=dt, iterations=res.iters,
                seconds_per_iteration=dt / max(res.iters, 1), status=res.status, relres=res.relres,

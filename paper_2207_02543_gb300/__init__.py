@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpod2g.so")
 
 OK, NOT_CONVERGED, BREAKDOWN, NOT_SPD, INVALID_ARG, ADMISSION, OOM, CUDA_ERROR, TIMEOUT, NONFINITE, PENDING = range(11)
 FP64, MIXED_FP32PHI, MIXED_BF16PHI = 0, 1, 2
+PCG, STATIONARY = 0, 1  # solution methods: Algorithm 3, or the two-grid cycle of Algorithm 2 iterated
 
 EXPORTS = [
     "pod2g_default_opts", "pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
@@ -37,7 +38,7 @@ class Pattern(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("omega", C.c_double), ("pre", C.c_int), ("post", C.c_int), ("precision", C.c_int),
                 ("beta_pr", C.c_int), ("max_batch", C.c_int), ("hbm_budget", C.c_size_t),
-                ("spin_limit", C.c_int64), ("chunk", C.c_int), ("stream", C.c_void_p)]
+                ("spin_limit", C.c_int64), ("chunk", C.c_int), ("stream", C.c_void_p), ("method", C.c_int)]
 
 
 _lib = None
@@ -116,7 +117,7 @@ class Solver:
     """One context: a shared block-CSR pattern, a POD basis Phi (n x k) and `max_batch` instance slots."""
 
     def __init__(self, row_ptr, col_idx, bs, phi, *, precision=MIXED_FP32PHI, omega=2.0 / 3.0, pre=1, post=1,
-                 beta_pr=False, max_batch=1, hbm_budget=0, chunk=8, spin_limit=0, stream=None):
+                 beta_pr=False, max_batch=1, hbm_budget=0, chunk=8, spin_limit=0, stream=None, method=0):
         lib = load_library()
         self._lib = lib
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -135,6 +136,7 @@ class Solver:
         o.beta_pr, o.max_batch, o.hbm_budget, o.chunk = int(beta_pr), max_batch, hbm_budget, chunk
         o.spin_limit = spin_limit
         o.stream = C.c_void_p(stream) if stream else None
+        o.method = method
         h = C.c_void_p()
         st = lib.pod2g_create(C.byref(pat), phi_cm.ctypes.data_as(C.POINTER(C.c_double)), k, C.byref(o), C.byref(h))
         if st != OK:

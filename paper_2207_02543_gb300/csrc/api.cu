@@ -82,6 +82,7 @@ void pod2g_default_opts(pod2g_opts* o) {
     o->spin_limit = 0;
     o->chunk = 8;
     o->stream = nullptr;
+    o->method = POD2G_PCG;
 }
 
 const char* pod2g_strerror(int s) {
@@ -144,6 +145,7 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
     if (o.precision < 0 || o.precision > 2 || o.max_batch < 1 || o.max_batch > POD2G_MAX_BP) return POD2G_INVALID_ARG;
     if (!(o.omega > 0.0) || o.pre < 0 || o.post < 0 || o.pre > 8 || o.post > 8) return POD2G_INVALID_ARG;
     if (o.precision != POD2G_FP64 && (o.pre > 1 || o.post > 1)) return POD2G_INVALID_ARG;
+    if (o.method != POD2G_PCG && o.method != POD2G_STATIONARY) return POD2G_INVALID_ARG;
     if (o.chunk <= 0) o.chunk = 8;
     // pattern checks: monotone row_ptr, columns in range and sorted, diagonal present
     const int nb = pat->n_brows;
@@ -174,6 +176,7 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
     c->precision = o.precision; c->pre = o.pre; c->post = o.post; c->beta_pr = o.beta_pr ? 1 : 0;
     c->B = o.max_batch; c->omega = o.omega; c->hbm_budget = o.hbm_budget; c->spin_limit = o.spin_limit;
     c->chunk = o.chunk;
+    c->method = o.method;
     int Bp = 1;
     while (Bp < o.max_batch) Bp <<= 1;
     c->Bp = c->precision == POD2G_FP64 ? 1 : Bp;

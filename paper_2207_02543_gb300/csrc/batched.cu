@@ -24,6 +24,9 @@
 // cluster through distributed shared memory, so the last cluster to finish sums
 // G/8 partial rows instead of G.
 //
+// The stationary method (Algorithm 2 iterated: u <- u + AMG(0; K, r), r <- r - K AMG(0; K, r))
+// runs the same kernels with alpha = 1 and beta = 0.
+//
 // One PCG iteration = 8 kernels, captured `chunk` times in one CUDA graph:
 //   k_p      p = s + beta p
 //   k_spmv   q = K p, p^T q             (last cluster: alpha = r^T s / p^T q, maxit, breakdown)
@@ -55,6 +58,7 @@ namespace {
 struct Dims {
     int nb, Bp, lgBp, k, kp, G, NP;  // NP = G / CLUSTER partial-sum rows of the row kernels
     int NPc;                         // partial-sum rows of the restriction
+    int stat;                        // 1: stationary two-grid iteration (alpha = 1, beta = 0)
     double omega;
 };
 
@@ -334,7 +338,7 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
             } else if (!(pq > 0.0) || !isfinite(pq)) {
                 s.state = SLOT_DONE; s.result = isfinite(pq) ? POD2G_BREAKDOWN : POD2G_NONFINITE; s.alpha = 0.0;
             } else {
-                s.alpha = s.rs / pq;
+                s.alpha = D.stat ? 1.0 : s.rs / pq;
                 s.iters += 1;
             }
         }
@@ -674,7 +678,7 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
                 S.state = SLOT_DONE;
                 S.result = isfinite(rs) ? POD2G_BREAKDOWN : POD2G_NONFINITE;
             } else {
-                S.beta = S.first ? 0.0 : (pr ? (rs - rsx) / S.rs : rs / S.rs);
+                S.beta = (S.first || D.stat) ? 0.0 : (pr ? (rs - rsx) / S.rs : rs / S.rs);
                 S.rs = rs;
                 S.first = 0;
                 if (want == SLOT_JOINING) S.state = SLOT_ACTIVE;
@@ -700,6 +704,7 @@ static Dims dims_of(pod2g_ctx* c) {
     D.G = c->grid_rows;
     D.NP = c->grid_rows / CLUSTER;
     D.NPc = restrict_grid(c) / CLUSTER;
+    D.stat = c->method == POD2G_STATIONARY;
     D.omega = c->omega;
     return D;
 }

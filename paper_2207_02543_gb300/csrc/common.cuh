@@ -48,6 +48,7 @@ struct pod2g_ctx {
     int device = 0;
     int nb = 0, bs = 0, n = 0, nnzb = 0, k = 0, kp = 0;   // kp: k padded to a multiple of 4
     int precision = 0, pre = 1, post = 1, beta_pr = 0, B = 1, Bp = 1, chunk = 8;
+    int method = 0;                     // POD2G_PCG or POD2G_STATIONARY
     double omega = 2.0 / 3.0;
     size_t hbm_budget = 0, allocated = 0;
     int64_t spin_limit = 0;

@@ -2,7 +2,8 @@
 // checked on the host after every iteration, no CUDA graphs. It is the direct
 // statement of Algorithm 3 (arXiv 2207.02543, Section 3.4) with the two-grid
 // cycle of Algorithm 2 (P = Phi_r, Section 3.3) and damped-Jacobi relaxation, in
-// FP64 throughout; it serves the FP64 workloads and is the baseline that the
+// FP64 throughout (or, as the stationary method, the two-grid cycle iterated on
+// its own); it serves the FP64 workloads and is the baseline that the
 // batched mixed-precision path is measured against.
 #include "common.cuh"
 
@@ -119,6 +120,11 @@ __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ s,
     for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x)
         p[d] = fma(beta, p[d], s[d]);
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BETA] = beta;
+}
+
+// x += s (the correction of one stationary two-grid cycle)
+__global__ void k_add(double* __restrict__ x, const double* __restrict__ s, int n) {
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) x[d] += s[d];
 }
 
 __global__ void k_copy_scalar(double* scal, int dst, int src) {
@@ -284,6 +290,27 @@ int plain_solve(pod2g_ctx* c, int slot, const double* b_dev, const double* x0_de
     }
     if (!std::isfinite(bb) || !std::isfinite(c->h_scal64[S_RR])) {
         status = POD2G_NONFINITE;
+    } else if (c->method == POD2G_STATIONARY) {
+        // Algorithm 2 as the solver: u <- u + AMG(0; K, f - K u, r1, r2), which is one
+        // two-grid cycle applied to u; the residual is recomputed from u every cycle.
+        const double tol2 = tol * tol * bb;
+        double rr = c->h_scal64[S_RR];
+        while (true) {
+            if (rr <= tol2) { status = POD2G_OK; break; }
+            if (k >= maxit) { status = POD2G_NOT_CONVERGED; break; }
+            P2G_TRY(plain_precond(c, slot, r, s));
+            k_add<<<G, T, 0, c->stream>>>(x, s, n);
+            P2G_TRY(pod2g_check_launch(c));
+            k_row<<<G, T, 0, c->stream>>>(ROW_RES, c->d_row_ptr, c->d_col_idx, vals, dinv, c->omega, x, b_dev, r,
+                                          c->nb, c->bs, nullptr, nullptr, nullptr);
+            P2G_TRY(pod2g_check_launch(c));
+            k_dot2<<<G, T, 0, c->stream>>>(r, r, nullptr, n, part, cnt, sc + S_RR, nullptr, nullptr, nullptr);
+            P2G_TRY(pod2g_check_launch(c));
+            P2G_TRY(read_scalars(c));
+            ++k;
+            rr = c->h_scal64[S_RR];
+            if (!std::isfinite(rr)) { status = POD2G_NONFINITE; break; }
+        }
     } else {
         const double tol2 = tol * tol * bb;
         double rr = c->h_scal64[S_RR];
