@@ -164,6 +164,16 @@ class StructuredProblem:
     def n_el(self) -> int:
         return int(self.centroids.shape[0])
 
+    @property
+    def npe(self) -> int:
+        """Nodes per element."""
+        return 2 ** self.dim
+
+    @property
+    def conn(self) -> np.ndarray:
+        """Element connectivity int32 [n_el, npe]: system node of each local node, -1 if eliminated."""
+        return np.ascontiguousarray(self._elem_nodes, dtype=np.int32)
+
     def values(self, coef: np.ndarray) -> np.ndarray:
         """Assemble values[nnzb, bs, bs] (float64) for element coefficients coef[n_el]."""
         coef = np.asarray(coef, dtype=np.float64)
