@@ -93,14 +93,16 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp):
+def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False):
     """Algorithmic HBM bytes per kernel of the batched iteration (values FP32, vectors
     double-float 8 B, s/y/D^-1 FP32 4 B, Phi FP32 read once per launch, col_idx
-    once per launch, per-slot scalars and partials negligible)."""
+    once per launch, per-slot scalars and partials negligible). Element operator:
+    per slot 4 B per element coefficient instead of the block values, plus the
+    8 B block descriptors and the row element lists once per launch."""
     P = wl.problem
     n, nnzb, bs = P.n, P.nnzb, P.bs
-    vals = nnzb * bs * bs * 4
-    pat = nnzb * 4 + (P.n_nodes + 1) * 4
+    vals = P.n_el * 4 if elements else nnzb * bs * bs * 4
+    pat = nnzb * 4 + (P.n_nodes + 1) * 4 + ((nnzb * 8 + P.n_nodes * 8 * 4) if elements else 0)
     phi = n * k_pad * 4
     per_lane = {  # bytes per active instance-iteration
         "k_p": n * (4 + 8 + 8),
@@ -121,9 +123,12 @@ def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp):
 # workload named (profiles/launches_q4_512_b64.md); valid only for the kernel
 # versions that capture measured.
 NCU_TRAFFIC = {
-    ("q4_512", 64): {"k_spmv": 3162.1e6, "k_smooth1": 3135.3e6, "k_post": 3156.3e6, "k_upd": 1569.0e6,
+    ("q4_512", 64, "assembled"): {"k_spmv": 3162.1e6, "k_smooth1": 3135.3e6, "k_post": 3156.3e6, "k_upd": 1569.0e6,
                      "k_restrict": 185.4e6, "k_prol": 568.0e6, "k_p": 615.7e6, "k_coarse": 0.8e6},
 }
+
+
+NCU_SOURCE = {("q4_512", 64, "assembled"): "profiles/launches_q4_512_b64.md"}
 
 
 def run_oracle(mode, inst, timeout=900, workload=WORKLOAD, tol=TOL, method="pcg"):
@@ -250,19 +255,26 @@ def gb300_arm(args):
     t_phi = time.time() - t0
     # instances of this replica: distinct per rank
     xis = wl.query_thetas(B, offset=replica_offset(rank, B))
-    vals = wl.values_torch(xis, device="cuda").reshape(B, -1).contiguous()      # FP64, resident in HBM
+    elements = args.operator == "elements"
+    if elements:   # FP64 element coefficients, resident in HBM
+        vals = torch.from_numpy(np.stack([wl.coef(xi) for xi in xis])).cuda()
+    else:          # FP64 assembled values, resident in HBM
+        vals = wl.values_torch(xis, device="cuda").reshape(B, -1).contiguous()
     b_dev = torch.from_numpy(wl.rhs(B, offset=replica_offset(rank, B))).cuda()
     x_dev = torch.empty_like(b_dev)
     stream = torch.cuda.Stream()
     precision = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
     method = pkg.STATIONARY if args.method == "stationary" else pkg.PCG
     tol, maxit = args.tol, args.maxit
+    el = dict(conn=P.conn, k_ref=P.Kref, fixed=P.clamped if P.dirichlet == "identity" else None) if elements else None
     s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=precision, omega=wl.spec.omega,
-                   max_batch=B, stream=stream.cuda_stream, method=method)
+                   max_batch=B, stream=stream.cuda_stream, method=method, elements=el)
     slots = list(range(B))
+    set_batch = s.set_coeffs_batch_dev if elements else s.set_values_batch_dev
+    set_one = s.set_coeffs if elements else s.set_values
 
     def step():
-        st, sts = s.set_values_batch_dev(slots, vals)
+        st, sts = set_batch(slots, vals)
         assert st == pkg.OK, pkg.strerror(st)
         iters, rel, status, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=tol, maxit=maxit)
         assert rc == pkg.OK, (pkg.strerror(rc), status)
@@ -272,7 +284,6 @@ def gb300_arm(args):
     for _ in range(max(args.warmup, 0)):
         iters, rel = step()
     sampler = ClockSampler(local)
-    s.kernel_timing(True)
     l0 = s.launch_count()
     if dist:
         dist.barrier()
@@ -291,6 +302,14 @@ def gb300_arm(args):
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = s.launch_count() - l0
+    # per-kernel CUDA-event times: separate, instrumented steps (event-record nodes
+    # inside the graph), outside the timed region above
+    s.kernel_timing(True)
+    lane_iters = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        iters, rel = step()
+        lane_iters += int(np.sum(iters))
+    torch.cuda.synchronize()
     ktimes = s.kernel_times()
     s.kernel_timing(False)
     ms = max_over_ranks(ms, dist)
@@ -302,7 +321,7 @@ def gb300_arm(args):
     G = max(1, min((P.n_nodes * Bp + 255) // 256, 4 * torch.cuda.get_device_properties(local).multi_processor_count))
     kp = {0: 0}.get(wl.spec.k, [v for v in (0, 8, 16, 24, 32, 40, 48, 64) if v >= wl.spec.k][0])
     nl = {k: v[1] for k, v in ktimes.items()}
-    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp)
+    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp, elements)
     rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     tot_k = sum(v[0] for v in ktimes.values())
@@ -310,8 +329,8 @@ def gb300_arm(args):
                 "frac": rates[dom] / peaks["hbm_gbs"], "peak_kind": peak_kind,
                 "bytes_per_launch": kb[dom] / max(nl[dom], 1),
                 "ms_per_launch": ktimes[dom][0] / max(nl[dom], 1),
-                "traffic": NCU_TRAFFIC.get((args.workload, B), {}).get(dom),
-                "traffic_source": "profiles/launches_q4_512_b64.md" if (args.workload, B) in NCU_TRAFFIC else None,
+                "traffic": NCU_TRAFFIC.get((args.workload, B, args.operator), {}).get(dom),
+                "traffic_source": NCU_SOURCE.get((args.workload, B, args.operator)),
                 "frac_vs_8TBs": rates[dom] / 8000.0,
                 "all_kernels": {k: {"share": ktimes[k][0] / tot_k, "GBs": round(rates[k], 1),
                                     "ms_per_launch": ktimes[k][0] / max(nl[k], 1)} for k in ktimes},
@@ -328,7 +347,7 @@ def gb300_arm(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             for i in slots:
-                assert s.set_values(i, vals_h[i]) == pkg.OK
+                assert set_one(i, vals_h[i]) == pkg.OK
             X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=tol, maxit=maxit)
             assert rc == pkg.OK
         e2e_s = (time.perf_counter() - t0) / e2e_steps
@@ -338,12 +357,13 @@ def gb300_arm(args):
         if not args.no_plain:
             sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1,
                             method=method)
+            vals_plain = vals if not elements else wl.values_torch(xis[:2], device="cuda").reshape(2, -1)
             nplain = 2
             times, its = [], []
             for i in range(nplain):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                assert sp.set_values(0, vals[i]) == pkg.OK
+                assert sp.set_values(0, vals_plain[i]) == pkg.OK
                 xp, itp, relp, stp = sp.solve(0, b_h[i], tol=tol, maxit=maxit)
                 torch.cuda.synchronize()
                 times.append(time.perf_counter() - t0)
@@ -378,8 +398,11 @@ def gb300_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
             "config": {"workload": workload_desc(wl, B, tol), "method": method_name(args.method),
+                       "operator": args.operator,
                        "batch": B, "n": P.n, "nnzb": P.nnzb, "k": wl.spec.k, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (4.8 GB FP64 values per step)",
+                       "l2": (f"inputs larger than L2 ({vals.numel() * 8 / 1e9:.2f} GB FP64 "
+                              f"{'coefficients' if elements else 'values'} per step; per-iteration working set "
+                              f"{P.n * B * 8 * 5 / 1e9:.2f} GB of vectors)"),
                        "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
                        "relres_max": float(np.max(rel)), "phi_setup_s": round(t_phi, 1)},
             "gpu_launches": int(launches / max(args.steps, 1)) if args.steps else 0,
@@ -440,6 +463,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="instances per step (default: the workload's batch)")
     ap.add_argument("--method", default="pcg", choices=["pcg", "stationary"],
                     help="pcg: Algorithm 3; stationary: the two-grid cycle of Algorithm 2 iterated on its own")
+    ap.add_argument("--operator", default="assembled", choices=["assembled", "elements"],
+                    help="instances as assembled block values, or as element coefficients (element-factored K)")
     ap.add_argument("--tol", type=float, default=TOL)
     ap.add_argument("--maxit", type=int, default=MAXIT)
     args = ap.parse_args()

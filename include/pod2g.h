@@ -119,7 +119,7 @@ int pod2g_create(const pod2g_pattern* pattern, const double* phi, int k,
  * its FP64 Cholesky factor. values: nnzb*bs*bs doubles, host memory if
  * on_device == 0, device memory otherwise. Returns POD2G_NOT_SPD for a
  * non-positive diagonal entry or an indefinite K_c (the slot is then unusable
- * until values are set again). */
+ * until values are set again). Not for element contexts (POD2G_INVALID_ARG). */
 int pod2g_set_values(pod2g_t ctx, int slot, const double* values, int on_device);
 
 /* Same for several slots at once: values_dev points to nslots consecutive
@@ -127,6 +127,44 @@ int pod2g_set_values(pod2g_t ctx, int slot, const double* values, int on_device)
  * each slot's set-up status; the return value is the first non-OK status. */
 int pod2g_set_values_batch_dev(pod2g_t ctx, int nslots, const int* slots,
                                const double* values_dev, int* status);
+
+/* ---- Element-factored operator.
+ * The finite-element systems of the paper (Section 4.1, Section 4.2) have a
+ * material coefficient constant over each element, so K(theta) = sum_e c_e(theta)
+ * K_ref scattered to the element's nodes, with one reference element matrix K_ref
+ * on a uniform mesh. A context created from this description stores per instance
+ * only the n_elems coefficients c_e instead of nnzb*bs*bs matrix values; its
+ * kernels form each block's values when they read it. Block (i, j) sums, over the
+ * elements e holding both node i (local index a) and node j (local index b), in
+ * ascending element index, the FP32 products c_e * K_ref[a, b] (c_e and K_ref
+ * rounded to FP32; each product and each partial sum rounded, no fused
+ * multiply-add). A fixed node's block row and column hold the identity on its
+ * diagonal block and zero elsewhere. The set-up (D^-1, K_c, Cholesky) uses these
+ * same FP32 values. */
+typedef struct {
+    int32_t n_elems;          /* number of elements */
+    int32_t npe;              /* nodes per element, 2..8; npe * bs <= 24 */
+    const int32_t* conn;      /* [n_elems][npe] block row (node) of each local node; -1 = no node */
+    const double* k_ref;      /* [(npe*bs) x (npe*bs)] row-major reference element matrix */
+    const uint8_t* fixed;     /* [n_brows] 1 = fixed node (identity row/column); NULL = none */
+} pod2g_elements;
+
+/* Like pod2g_create, for a pattern whose blocks hold element contributions as
+ * described above (host arrays, copied). Mixed precision modes only (FP64 returns
+ * POD2G_INVALID_ARG), and so is a node with more than 8 adjacent elements, an
+ * element whose node pair has no stored block, a node listed twice in one
+ * element, or a non-symmetric K_ref. */
+int pod2g_create_elements(const pod2g_pattern* pattern, const pod2g_elements* elements,
+                          const double* phi, int k, const pod2g_opts* opts, pod2g_t* out);
+
+/* Element contexts: load one instance's n_elems coefficients c_e into a slot
+ * (host memory if on_device == 0, else device memory) and run its set-up, with
+ * the same status rules as pod2g_set_values (non-finite c_e: POD2G_NONFINITE). */
+int pod2g_set_coeffs(pod2g_t ctx, int slot, const double* coeffs, int on_device);
+
+/* Several slots at once: coeffs_dev holds nslots * n_elems doubles (device). */
+int pod2g_set_coeffs_batch_dev(pod2g_t ctx, int nslots, const int* slots,
+                               const double* coeffs_dev, int* status);
 
 /* Solve one instance (Algorithm 3). b, x0 (NULL: zero) and x are host arrays of
  * n doubles. iters / relres may be NULL. */
@@ -156,7 +194,9 @@ int pod2g_solve_batch_dev(pod2g_t ctx, int nslots, const int* slots, const doubl
 int pod2g_serve_start(pod2g_t ctx, int max_queue);
 int pod2g_submit(pod2g_t ctx, const double* values, const double* b, const double* x0,
                  double tol, int maxit, uint64_t* ticket);
-/* Non-blocking: POD2G_PENDING until the request finishes; then copies x (host, n
+/* (For a context from pod2g_create_elements, `values` holds the request's n_elems
+ * coefficients.)
+ * Non-blocking: POD2G_PENDING until the request finishes; then copies x (host, n
  * doubles; may be NULL), iters, relres, status (may be NULL), returns OK and
  * forgets the ticket. latency_s (may be NULL) = submit-to-completion seconds. */
 int pod2g_poll(pod2g_t ctx, uint64_t ticket, double* x, int* iters, double* relres,

@@ -23,7 +23,8 @@ EXPORTS = [
     "pod2g_default_opts", "pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
     "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
     "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_kernel_timing", "pod2g_kernel_times",
-    "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc", "pod2g_device_bytes",
+    "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc", "pod2g_device_bytes", "pod2g_create_elements",
+    "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
 ]
 NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
 TOO_LARGE = 11
@@ -33,6 +34,11 @@ KERNEL_NAMES = ["k_p", "k_spmv", "k_upd", "k_smooth1", "k_restrict", "k_coarse",
 class Pattern(C.Structure):
     _fields_ = [("n_brows", C.c_int32), ("bs", C.c_int32), ("row_ptr", C.POINTER(C.c_int32)),
                 ("col_idx", C.POINTER(C.c_int32))]
+
+
+class Elements(C.Structure):
+    _fields_ = [("n_elems", C.c_int32), ("npe", C.c_int32), ("conn", C.POINTER(C.c_int32)),
+                ("k_ref", C.POINTER(C.c_double)), ("fixed", C.POINTER(C.c_uint8))]
 
 
 class Opts(C.Structure):
@@ -58,6 +64,10 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_default_opts.argtypes = [C.POINTER(Opts)]
     lib.pod2g_default_opts.restype = None
     lib.pod2g_create.argtypes = [C.POINTER(Pattern), DP, I, C.POINTER(Opts), C.POINTER(P)]
+    lib.pod2g_create_elements.argtypes = [C.POINTER(Pattern), C.POINTER(Elements), DP, I, C.POINTER(Opts),
+                                          C.POINTER(P)]
+    lib.pod2g_set_coeffs.argtypes = [P, I, P, I]
+    lib.pod2g_set_coeffs_batch_dev.argtypes = [P, I, IP, P, IP]
     lib.pod2g_set_values.argtypes = [P, I, P, I]
     lib.pod2g_set_values_batch_dev.argtypes = [P, I, IP, P, IP]
     lib.pod2g_solve.argtypes = [P, I, DP, DP, D, I, DP, IP, DP]
@@ -83,7 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_destroy.restype = None
     lib.pod2g_strerror.argtypes = [I]
     lib.pod2g_strerror.restype = C.c_char_p
-    for name in ("pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
+    for name in ("pod2g_create", "pod2g_create_elements", "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
+                 "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
                  "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
                  "pod2g_serve_stop", "pod2g_info"):
         getattr(lib, name).restype = C.c_int
@@ -117,7 +128,11 @@ class Solver:
     """One context: a shared block-CSR pattern, a POD basis Phi (n x k) and `max_batch` instance slots."""
 
     def __init__(self, row_ptr, col_idx, bs, phi, *, precision=MIXED_FP32PHI, omega=2.0 / 3.0, pre=1, post=1,
-                 beta_pr=False, max_batch=1, hbm_budget=0, chunk=8, spin_limit=0, stream=None, method=0):
+                 beta_pr=False, max_batch=1, hbm_budget=0, chunk=8, spin_limit=0, stream=None, method=0,
+                 elements=None):
+        """elements: None (instances are given as assembled block values), or a dict with
+        conn [n_el, npe] int, k_ref [(npe*bs)^2] float64 and optional fixed [n_brows] bool:
+        the element-factored operator, instances given as element coefficients."""
         lib = load_library()
         self._lib = lib
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -138,9 +153,24 @@ class Solver:
         o.stream = C.c_void_p(stream) if stream else None
         o.method = method
         h = C.c_void_p()
-        st = lib.pod2g_create(C.byref(pat), phi_cm.ctypes.data_as(C.POINTER(C.c_double)), k, C.byref(o), C.byref(h))
+        if elements is None:
+            st = lib.pod2g_create(C.byref(pat), phi_cm.ctypes.data_as(C.POINTER(C.c_double)), k, C.byref(o),
+                                  C.byref(h))
+            self.inst_len = int(self.row_ptr[-1]) * bs * bs
+        else:
+            conn = np.ascontiguousarray(elements["conn"], dtype=np.int32)
+            kref = np.ascontiguousarray(elements["k_ref"], dtype=np.float64)
+            fixed = elements.get("fixed")
+            fixed = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+            el = Elements(conn.shape[0], conn.shape[1], conn.ctypes.data_as(C.POINTER(C.c_int32)),
+                          kref.ctypes.data_as(C.POINTER(C.c_double)),
+                          fixed.ctypes.data_as(C.POINTER(C.c_uint8)) if fixed is not None else None)
+            st = lib.pod2g_create_elements(C.byref(pat), C.byref(el), phi_cm.ctypes.data_as(C.POINTER(C.c_double)),
+                                           k, C.byref(o), C.byref(h))
+            self.inst_len = conn.shape[0]
+        self.elements = elements is not None
         if st != OK:
-            raise Pod2gError(st, "pod2g_create")
+            raise Pod2gError(st, "pod2g_create_elements" if elements is not None else "pod2g_create")
         self.h = h
         self.k, self.bs, self.max_batch, self.precision = k, bs, max_batch, precision
         self.nnzb = int(self.row_ptr[-1])
@@ -176,15 +206,43 @@ class Solver:
     def set_values(self, slot: int, values) -> int:
         """values: numpy float64 (host) or a CUDA float64 tensor, nnzb*bs*bs entries."""
         if _is_cuda(values):
+            if values.numel() != self.inst_len:
+                return INVALID_ARG
             st = self._lib.pod2g_set_values(self.h, slot, C.c_void_p(values.data_ptr()), 1)
         else:
             v = _f64(values).reshape(-1)
+            if v.size != self.inst_len:
+                return INVALID_ARG
             st = self._lib.pod2g_set_values(self.h, slot, v.ctypes.data_as(C.c_void_p), 0)
         return st
+
+    def set_coeffs(self, slot: int, coeffs) -> int:
+        """Element contexts: coeffs, numpy float64 (host) or a CUDA float64 tensor, n_elems entries."""
+        if _is_cuda(coeffs):
+            if coeffs.numel() != self.inst_len:
+                return INVALID_ARG
+            return self._lib.pod2g_set_coeffs(self.h, slot, C.c_void_p(coeffs.data_ptr()), 1)
+        v = _f64(coeffs).reshape(-1)
+        if v.size != self.inst_len:
+            return INVALID_ARG
+        return self._lib.pod2g_set_coeffs(self.h, slot, v.ctypes.data_as(C.c_void_p), 0)
+
+    def set_coeffs_batch_dev(self, slots, coeffs_dev):
+        """coeffs_dev: CUDA float64 tensor [len(slots), n_elems]."""
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        status = np.zeros(len(slots), dtype=np.int32)
+        if coeffs_dev.numel() != len(slots) * self.inst_len:
+            return INVALID_ARG, status
+        st = self._lib.pod2g_set_coeffs_batch_dev(self.h, len(slots), slots.ctypes.data_as(C.POINTER(C.c_int)),
+                                                  C.c_void_p(coeffs_dev.data_ptr()),
+                                                  status.ctypes.data_as(C.POINTER(C.c_int)))
+        return st, status
 
     def set_values_batch_dev(self, slots, values_dev):
         slots = np.ascontiguousarray(slots, dtype=np.int32)
         status = np.zeros(len(slots), dtype=np.int32)
+        if values_dev.numel() != len(slots) * self.inst_len:
+            return INVALID_ARG, status
         st = self._lib.pod2g_set_values_batch_dev(self.h, len(slots), slots.ctypes.data_as(C.POINTER(C.c_int)),
                                                   C.c_void_p(values_dev.data_ptr()),
                                                   status.ctypes.data_as(C.POINTER(C.c_int)))
@@ -242,8 +300,11 @@ class Solver:
             raise Pod2gError(st, "pod2g_serve_start")
 
     def submit(self, values, b, x0=None, tol=1e-8, maxit=1000):
+        """values: the instance's block values, or its element coefficients for an element context."""
         v = _f64(values).reshape(-1)
         b = _f64(b)
+        if v.size != self.inst_len or b.size != self.n or (x0 is not None and np.size(x0) != self.n):
+            return INVALID_ARG, 0
         x0a = _f64(x0) if x0 is not None else None
         t = C.c_uint64(0)
         st = self._lib.pod2g_submit(self.h, _dptr(v), _dptr(b), _dptr(x0a) if x0a is not None else None, tol, maxit,

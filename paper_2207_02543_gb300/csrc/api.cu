@@ -109,7 +109,7 @@ static void free_all(pod2g_ctx* c) {
                     c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
                     c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
                     c->d_pdf, c->d_qdf, c->d_bdf, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
-                    c->d_mask, c->d_iob, c->d_iox, c->d_err};
+                    c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_scal64) cudaFreeHost(c->h_scal64);
@@ -134,7 +134,77 @@ void pod2g_destroy(pod2g_ctx* c) {
         if (s_ != POD2G_OK) { free_all(c); delete c; return s_; }              \
     } while (0)
 
-int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g_opts* opts_in, pod2g_t* out) {
+}  // extern "C"
+
+// Host tables of the element-factored operator (see ElemOp): per block row its
+// adjacent elements in ascending index, per stored block its descriptor, and the
+// FP32 reference sub-blocks. Returns INVALID_ARG for a description the solver
+// cannot represent.
+static int build_element_tables(const pod2g_pattern* pat, const pod2g_elements* el, std::vector<int32_t>& rowel,
+                                std::vector<uint64_t>& desc, std::vector<float>& kref) {
+    const int nb = pat->n_brows, bs = pat->bs, npe = el->npe;
+    if (el->n_elems < 1 || npe < 2 || npe > 8 || npe * bs > 24 || !el->conn || !el->k_ref) return POD2G_INVALID_ARG;
+    const int nk = npe * bs;
+    double kmax = 0.0;
+    for (int t = 0; t < nk * nk; ++t) {
+        if (!std::isfinite(el->k_ref[t])) return POD2G_NONFINITE;
+        kmax = std::max(kmax, std::fabs(el->k_ref[t]));
+    }
+    for (int r = 0; r < nk; ++r)
+        for (int q = 0; q < r; ++q)
+            if (std::fabs(el->k_ref[r * nk + q] - el->k_ref[q * nk + r]) > 1e-12 * kmax) return POD2G_INVALID_ARG;
+    rowel.assign((size_t)nb * POD2G_ELEM_RE, -1);
+    std::vector<int> cnt(nb, 0);
+    for (int e = 0; e < el->n_elems; ++e) {
+        const int32_t* cn = el->conn + (size_t)e * npe;
+        for (int a = 0; a < npe; ++a) {
+            const int i = cn[a];
+            if (i < -1 || i >= nb) return POD2G_INVALID_ARG;
+            if (i < 0) continue;
+            for (int b = 0; b < a; ++b)
+                if (cn[b] == i) return POD2G_INVALID_ARG;  // a node listed twice
+            if (cnt[i] >= POD2G_ELEM_RE) return POD2G_INVALID_ARG;
+            rowel[(size_t)i * POD2G_ELEM_RE + cnt[i]++] = e;  // e ascends: lists are sorted
+        }
+    }
+    const int64_t nnzb = pat->row_ptr[nb];
+    desc.assign((size_t)nnzb, 0ull);
+    for (int i = 0; i < nb; ++i) {
+        const int32_t* cols = pat->col_idx + pat->row_ptr[i];
+        const int ncol = pat->row_ptr[i + 1] - pat->row_ptr[i];
+        for (int p = 0; p < cnt[i]; ++p) {
+            const int e = rowel[(size_t)i * POD2G_ELEM_RE + p];
+            const int32_t* cn = el->conn + (size_t)e * npe;
+            int a = 0;
+            while (cn[a] != i) ++a;
+            for (int b = 0; b < npe; ++b) {
+                const int j = cn[b];
+                if (j < 0) continue;
+                const int32_t* hit = std::lower_bound(cols, cols + ncol, j);
+                if (hit == cols + ncol || *hit != j) return POD2G_INVALID_ARG;  // coupling without a stored block
+                uint64_t& d = desc[(size_t)(pat->row_ptr[i] + (hit - cols))];
+                d |= (1ull << (48 + p)) | ((uint64_t)(a * npe + b) << (6 * p));
+            }
+        }
+    }
+    if (el->fixed) {
+        for (int i = 0; i < nb; ++i)
+            for (int t = pat->row_ptr[i]; t < pat->row_ptr[i + 1]; ++t) {
+                const int j = pat->col_idx[t];
+                if (el->fixed[i] || el->fixed[j]) desc[t] = (i == j && el->fixed[i]) ? (1ull << 63) : (1ull << 62);
+            }
+    }
+    kref.assign((size_t)npe * npe * bs * bs, 0.f);
+    for (int a = 0; a < npe; ++a)
+        for (int b = 0; b < npe; ++b)
+            for (int r = 0; r < bs; ++r)
+                for (int q = 0; q < bs; ++q)
+                    kref[((size_t)(a * npe + b) * bs + r) * bs + q] = (float)el->k_ref[(a * bs + r) * nk + b * bs + q];
+    return POD2G_OK;
+}
+
+static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const double* phi, int k,
+                       const pod2g_opts* opts_in, pod2g_t* out) {
     if (!out) return POD2G_INVALID_ARG;
     *out = nullptr;
     pod2g_opts o;
@@ -169,6 +239,14 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
         for (long long e = 0; e < n * k; ++e)
             if (!std::isfinite(phi[e])) return POD2G_NONFINITE;
     }
+    std::vector<int32_t> h_rowel;
+    std::vector<uint64_t> h_desc;
+    std::vector<float> h_kref;
+    if (el) {
+        if (o.precision == POD2G_FP64) return POD2G_INVALID_ARG;
+        int st = build_element_tables(pat, el, h_rowel, h_desc, h_kref);
+        if (st != POD2G_OK) return st;
+    }
 
     pod2g_ctx* c = new pod2g_ctx();
     cudaGetDevice(&c->device);
@@ -177,6 +255,11 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
     c->B = o.max_batch; c->omega = o.omega; c->hbm_budget = o.hbm_budget; c->spin_limit = o.spin_limit;
     c->chunk = o.chunk;
     c->method = o.method;
+    if (el) {
+        c->elem = 1;
+        c->n_el = el->n_elems;
+        c->npe = el->npe;
+    }
     int Bp = 1;
     while (Bp < o.max_batch) Bp <<= 1;
     c->Bp = c->precision == POD2G_FP64 ? 1 : Bp;
@@ -198,7 +281,7 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
     ALLOC(c->d_diag_blk, sizeof(int32_t) * nb);
     ALLOC(c->d_Lc, sizeof(double) * std::max(1, c->B * k * k));
     ALLOC(c->d_setup_status, sizeof(int) * c->B);
-    ALLOC(c->d_stage, sizeof(double) * tot);
+    ALLOC(c->d_stage, sizeof(double) * std::max(tot, (long long)c->n_el));
     ALLOC(c->d_W, sizeof(double) * std::max(1LL, n * kp));
     ALLOC(c->d_ac_part, sizeof(double) * std::max(1, 2 * c->num_sms * k * k));
     ALLOC(c->d_Ac, sizeof(double) * std::max(1, k * k));
@@ -218,7 +301,14 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
     } else {
         ALLOC(c->d_phi32, sizeof(float) * std::max(1LL, n * kp));
         ALLOC(c->d_stage32, sizeof(float) * tot);
-        ALLOC(c->d_vals32, sizeof(float) * tot * Bp);
+        if (c->elem) {
+            ALLOC(c->d_desc, sizeof(uint64_t) * nnzb);
+            ALLOC(c->d_rowel, sizeof(int32_t) * nb * POD2G_ELEM_RE);
+            ALLOC(c->d_kref32, sizeof(float) * h_kref.size());
+            ALLOC(c->d_coef32, sizeof(float) * (size_t)c->n_el * Bp);
+        } else {
+            ALLOC(c->d_vals32, sizeof(float) * tot * Bp);
+        }
         ALLOC(c->d_dinv32, sizeof(float) * n * Bp);
         ALLOC(c->d_xdf, sizeof(float2) * n * Bp);
         ALLOC(c->d_rdf, sizeof(float2) * n * Bp);
@@ -264,10 +354,16 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
             ok = up(c->d_phi32, h.data(), sizeof(float) * n * kp);
         }
     }
+    if (ok && c->elem) {
+        ok = up(c->d_desc, h_desc.data(), sizeof(uint64_t) * nnzb) &&
+             up(c->d_rowel, h_rowel.data(), sizeof(int32_t) * nb * POD2G_ELEM_RE) &&
+             up(c->d_kref32, h_kref.data(), sizeof(float) * h_kref.size()) &&
+             cudaMemset(c->d_coef32, 0, sizeof(float) * (size_t)c->n_el * Bp) == cudaSuccess;
+    }
     if (ok && c->precision != POD2G_FP64) {
         ok = cudaMemset(c->d_sc, 0, sizeof(SlotScalars) * Bp) == cudaSuccess &&
              cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
-             cudaMemset(c->d_vals32, 0, sizeof(float) * tot * Bp) == cudaSuccess &&
+             (c->elem || cudaMemset(c->d_vals32, 0, sizeof(float) * tot * Bp) == cudaSuccess) &&
              cudaMemset(c->d_dinv32, 0, sizeof(float) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_xdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_rdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
@@ -285,6 +381,19 @@ int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g
     }
     *out = c;
     return POD2G_OK;
+}
+
+extern "C" {
+
+int pod2g_create(const pod2g_pattern* pat, const double* phi, int k, const pod2g_opts* opts, pod2g_t* out) {
+    return create_impl(pat, nullptr, phi, k, opts, out);
+}
+
+int pod2g_create_elements(const pod2g_pattern* pat, const pod2g_elements* el, const double* phi, int k,
+                          const pod2g_opts* opts, pod2g_t* out) {
+    if (out) *out = nullptr;
+    if (!el) return POD2G_INVALID_ARG;
+    return create_impl(pat, el, phi, k, opts, out);
 }
 
 int pod2g_info(pod2g_t c, int* n, int* nnzb, int* k, int* max_batch) {
@@ -331,7 +440,7 @@ static int finish_setup(pod2g_ctx* c, int nslots, const int* slots, int* status)
 
 int pod2g_set_values(pod2g_t c, int slot, const double* values, int on_device) {
     if (!c || !values || slot < 0 || slot >= c->B) return POD2G_INVALID_ARG;
-    if (c->serving) return POD2G_INVALID_ARG;
+    if (c->serving || c->elem) return POD2G_INVALID_ARG;
     const size_t bytes = sizeof(double) * (size_t)c->nnzb * c->bs * c->bs;
     const double* src = values;
     if (!on_device) {
@@ -343,9 +452,33 @@ int pod2g_set_values(pod2g_t c, int slot, const double* values, int on_device) {
     return finish_setup(c, 1, &slot, nullptr);
 }
 
+int pod2g_set_coeffs(pod2g_t c, int slot, const double* coeffs, int on_device) {
+    if (!c || !coeffs || slot < 0 || slot >= c->B) return POD2G_INVALID_ARG;
+    if (c->serving || !c->elem) return POD2G_INVALID_ARG;
+    const double* src = coeffs;
+    if (!on_device) {
+        P2G_CUDA(cudaMemcpyAsync(c->d_stage, coeffs, sizeof(double) * c->n_el, cudaMemcpyHostToDevice, c->stream));
+        src = c->d_stage;
+    }
+    c->setup_ok[slot] = 0;
+    P2G_TRY(setup_coeffs(c, slot, src));
+    return finish_setup(c, 1, &slot, nullptr);
+}
+
+int pod2g_set_coeffs_batch_dev(pod2g_t c, int nslots, const int* slots, const double* coeffs_dev, int* status) {
+    if (!c || !slots || !coeffs_dev || nslots < 1 || nslots > c->B) return POD2G_INVALID_ARG;
+    if (c->serving || !c->elem) return POD2G_INVALID_ARG;
+    for (int i = 0; i < nslots; ++i) {
+        if (slots[i] < 0 || slots[i] >= c->B) return POD2G_INVALID_ARG;
+        c->setup_ok[slots[i]] = 0;
+        P2G_TRY(setup_coeffs(c, slots[i], coeffs_dev + (size_t)i * c->n_el));
+    }
+    return finish_setup(c, nslots, slots, status);
+}
+
 int pod2g_set_values_batch_dev(pod2g_t c, int nslots, const int* slots, const double* values_dev, int* status) {
     if (!c || !slots || !values_dev || nslots < 1 || nslots > c->B) return POD2G_INVALID_ARG;
-    if (c->serving) return POD2G_INVALID_ARG;
+    if (c->serving || c->elem) return POD2G_INVALID_ARG;
     const size_t tot = (size_t)c->nnzb * c->bs * c->bs;
     for (int i = 0; i < nslots; ++i) {
         if (slots[i] < 0 || slots[i] >= c->B) return POD2G_INVALID_ARG;

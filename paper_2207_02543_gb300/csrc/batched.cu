@@ -162,6 +162,15 @@ __device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, 
     }
 }
 
+// Element kernels (MF = 1) stage the FP32 reference sub-blocks in shared memory
+// (read with warp-uniform addresses); assembled kernels read per-slot values.
+#define ELEM_SMEM_KREF(MF, E)                                                    \
+    __shared__ float s_kref[(MF) ? POD2G_KREF_MAX : 1];                          \
+    if (MF) {                                                                    \
+        for (int t_ = threadIdx.x; t_ < (E).nk; t_ += blockDim.x) s_kref[t_] = (E).kref[t_]; \
+        __syncthreads();                                                         \
+    }
+
 // ---------------------------------------------------------------------------- load / store / residual
 // Joining lanes: b -> bdf, x0 -> xdf (zero if absent), p = q = 0.
 __global__ void k_load(const double* __restrict__ b, const double* __restrict__ x0, const int* __restrict__ slots,
@@ -197,13 +206,14 @@ __global__ void k_store(double* __restrict__ x, const int* __restrict__ slots, i
 // r = b - K x in double-float for masked lanes. init: writes r, sums ||b||^2 and
 // sets tol2 = tol^2 ||b||^2 (b = 0 or non-finite -> DONE). final: sums
 // ||b - K x||^2 into relres.
-template <int BS>
+template <int BS, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __restrict__ row_ptr,
-        const int32_t* __restrict__ col_idx, const float* __restrict__ vals, const float2* __restrict__ x,
+        const int32_t* __restrict__ col_idx, const float* __restrict__ vals, ElemOp E, const float2* __restrict__ x,
         const float2* __restrict__ b, float2* __restrict__ r, double* part, unsigned* counter, SlotScalars* sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[2 * POD2G_MAX_BP];
+    ELEM_SMEM_KREF(MF, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = mask[lane] != 0;
     float bh = 0.f, bl = 0.f, rh = 0.f, rl = 0.f;
@@ -217,15 +227,23 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
             for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
             float2 xj[UNROLL][BS];
             float v[UNROLL][BS * BS];
+            uint64_t dsc[UNROLL];
+            float ce[MF ? POD2G_ELEM_RE : 1];
+            if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
                 [&](int u, int blk, int j) {
 #pragma unroll
                     for (int cc = 0; cc < BS; ++cc) xj[u][cc] = x[((long long)j * BS + cc) * D.Bp + lane];
-                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+                    if constexpr (MF) {
+                        dsc[u] = __ldg(E.desc + blk);
+                    } else {
+                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                    for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                    }
                 },
                 [&](int u) {
+                    if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                     for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -279,13 +297,14 @@ __global__ void k_p(Dims D, int want, const float* __restrict__ s, float2* __res
 }
 
 // q = K p (double-float), partial p^T q; last cluster: alpha per slot.
-template <int BS>
+template <int BS, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-       const float* __restrict__ vals, const float2* __restrict__ p, float2* __restrict__ q, double* part,
+       const float* __restrict__ vals, ElemOp E, const float2* __restrict__ p, float2* __restrict__ q, double* part,
        unsigned* counter, SlotScalars* sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[POD2G_MAX_BP];
+    ELEM_SMEM_KREF(MF, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float dh = 0.f, dl = 0.f;
@@ -299,15 +318,23 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
             for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
             float2 pj[UNROLL][BS];
             float v[UNROLL][BS * BS];
+            uint64_t dsc[UNROLL];
+            float ce[MF ? POD2G_ELEM_RE : 1];
+            if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
                 [&](int u, int blk, int j) {
 #pragma unroll
                     for (int cc = 0; cc < BS; ++cc) pj[u][cc] = p[((long long)j * BS + cc) * D.Bp + lane];
-                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+                    if constexpr (MF) {
+                        dsc[u] = __ldg(E.desc + blk);
+                    } else {
+                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                    for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                    }
                 },
                 [&](int u) {
+                    if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                     for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -364,13 +391,14 @@ __global__ void k_upd(Dims D, int want, float2* __restrict__ x, float2* __restri
 // Pre-relaxation from zero and the residual it leaves: y1 = omega D^-1 r (r1 = 1)
 // or 0 (r1 = 0), r1 = r - K y1, written to out (FP32); cluster partial sums of
 // ||r||^2 go to part[cluster][slot].
-template <int BS>
+template <int BS, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-          const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ r,
+          const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
           float* __restrict__ out, double* part, const SlotScalars* __restrict__ sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[POD2G_MAX_BP];
+    ELEM_SMEM_KREF(MF, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float rr = 0.f;
@@ -385,6 +413,9 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
             for (int a = 0; a < BS; ++a) acc[a] = 0.f;
             if (PRE) {
                 float yj[UNROLL][BS], v[UNROLL][BS * BS];
+                uint64_t dsc[UNROLL];
+                float ce[MF ? POD2G_ELEM_RE : 1];
+                if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
                     [&](int u, int blk, int j) {
 #pragma unroll
@@ -392,11 +423,16 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
                             const long long o = ((long long)j * BS + cc) * D.Bp + lane;
                             yj[u][cc] = w * dinv[o] * r[o].x;
                         }
-                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+                        if constexpr (MF) {
+                            dsc[u] = __ldg(E.desc + blk);
+                        } else {
+                            const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                            for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                        }
                     },
                     [&](int u) {
+                        if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                         for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -614,13 +650,14 @@ k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restric
 
 // s = y2 + omega D^-1 (r - K y2) (r2 = 1) or y2 (r2 = 0); partial r^T s (and
 // r^T s_old for Polak-Ribiere); last cluster: beta, JOINING -> ACTIVE.
-template <int BS, int POST>
+template <int BS, int POST, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-       const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ r,
+       const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
        const float* __restrict__ y, float* __restrict__ s, double* part, unsigned* counter, SlotScalars* sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[2 * POD2G_MAX_BP];
+    ELEM_SMEM_KREF(MF && POST, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float h = 0.f, l = 0.f, xh = 0.f, xl = 0.f;
@@ -635,15 +672,23 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
             for (int a = 0; a < BS; ++a) acc[a] = 0.f;
             if (POST) {
                 float yj[UNROLL][BS], v[UNROLL][BS * BS];
+                uint64_t dsc[UNROLL];
+                float ce[MF ? POD2G_ELEM_RE : 1];
+                if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
                     [&](int u, int blk, int j) {
 #pragma unroll
                         for (int cc = 0; cc < BS; ++cc) yj[u][cc] = y[((long long)j * BS + cc) * D.Bp + lane];
-                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+                        if constexpr (MF) {
+                            dsc[u] = __ldg(E.desc + blk);
+                        } else {
+                            const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
-                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                            for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                        }
                     },
                     [&](int u) {
+                        if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                         for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -716,19 +761,27 @@ int batched_grid(int num_sms, long long items) {
     return ceil_div(g, CLUSTER) * CLUSTER;
 }
 
+// KERNEL<BS, MF> for the context's block size and operator form (MF = 1: element-factored)
 #define LAUNCH_BS(KERNEL, ...)                                                         \
     do {                                                                               \
-        if (c->bs == 1) KERNEL<1> __VA_ARGS__;                                         \
-        else if (c->bs == 2) KERNEL<2> __VA_ARGS__;                                    \
-        else KERNEL<3> __VA_ARGS__;                                                    \
+        if (c->elem) {                                                                 \
+            if (c->bs == 1) KERNEL<1, 1> __VA_ARGS__;                                  \
+            else if (c->bs == 2) KERNEL<2, 1> __VA_ARGS__;                             \
+            else KERNEL<3, 1> __VA_ARGS__;                                             \
+        } else {                                                                       \
+            if (c->bs == 1) KERNEL<1, 0> __VA_ARGS__;                                  \
+            else if (c->bs == 2) KERNEL<2, 0> __VA_ARGS__;                             \
+            else KERNEL<3, 0> __VA_ARGS__;                                             \
+        }                                                                              \
     } while (0)
 
 #define KP_LIST(X) X(8) X(16) X(24) X(32) X(40) X(48) X(64)
 
-template <int BS>
+template <int BS, int MF>
 static void launch_smooth1(pod2g_ctx* c, Dims D, int want) {
-    k_smooth1<BS><<<D.G, POD2G_THREADS, 0, c->stream>>>(D, want, c->pre, c->d_row_ptr, c->d_col_idx, c->d_vals32,
-                                                         c->d_dinv32, c->d_rdf, c->d_y32, c->d_part, c->d_sc);
+    k_smooth1<BS, MF><<<D.G, POD2G_THREADS, 0, c->stream>>>(D, want, c->pre, c->d_row_ptr, c->d_col_idx,
+                                                             c->d_vals32, elem_op(c), c->d_dinv32, c->d_rdf,
+                                                             c->d_y32, c->d_part, c->d_sc);
 }
 
 // slots per thread of the restriction: 4 (vector loads), more when Bp x kp needs it
@@ -787,17 +840,17 @@ static void launch_prol(pod2g_ctx* c, Dims D, int want) {
 #undef CASE_KP
 }
 
-template <int BS>
+template <int BS, int MF>
 static void launch_post(pod2g_ctx* c, Dims D, int want) {
     dim3 g(D.G), t(POD2G_THREADS);
     if (c->post)
-        k_post<BS, 1><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
-                                              c->d_dinv32, c->d_rdf, c->d_y32, c->d_s32, c->d_part,
-                                              c->d_counters + CNT_POST, c->d_sc);
+        k_post<BS, 1, MF><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
+                                                  elem_op(c), c->d_dinv32, c->d_rdf, c->d_y32, c->d_s32, c->d_part,
+                                                  c->d_counters + CNT_POST, c->d_sc);
     else
-        k_post<BS, 0><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
-                                              c->d_dinv32, c->d_rdf, c->d_y32, c->d_s32, c->d_part,
-                                              c->d_counters + CNT_POST, c->d_sc);
+        k_post<BS, 0, MF><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
+                                                  elem_op(c), c->d_dinv32, c->d_rdf, c->d_y32, c->d_s32, c->d_part,
+                                                  c->d_counters + CNT_POST, c->d_sc);
 }
 
 // Event-record node after a kernel of a captured iteration (timing mode only).
@@ -833,8 +886,9 @@ static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     if (c->cap_ev) P2G_CUDA(cudaEventRecordWithFlags(c->cap_ev[c->cap_idx++], c->stream, cudaEventRecordExternal));
     k_p<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_s32, c->d_pdf, c->d_sc, total);
     P2G_TRY(mark(c));
+    const ElemOp E = elem_op(c);
     LAUNCH_BS(k_spmv, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx, c->d_vals32,
-                                                             c->d_pdf, c->d_qdf, c->d_part,
+                                                             E, c->d_pdf, c->d_qdf, c->d_part,
                                                              c->d_counters + CNT_SPMV, c->d_sc));
     P2G_TRY(mark(c));
     k_upd<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_xdf, c->d_rdf, c->d_pdf, c->d_qdf, c->d_sc, total);
@@ -901,8 +955,9 @@ int batched_load(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev
     k_load<<<elementwise_grid(c, tot), POD2G_THREADS, 0, c->stream>>>(
         b_dev, x0_dev, d_slots, nslots, c->n, c->Bp, c->d_bdf, c->d_xdf, c->d_pdf, c->d_qdf, c->d_s32);
     P2G_TRY(pod2g_check_launch(c));
+    const ElemOp E = elem_op(c);
     LAUNCH_BS(k_resid, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, 0, c->d_mask, c->d_row_ptr, c->d_col_idx,
-                                                              c->d_vals32, c->d_xdf, c->d_bdf, c->d_rdf, c->d_part,
+                                                              c->d_vals32, E, c->d_xdf, c->d_bdf, c->d_rdf, c->d_part,
                                                               c->d_counters + CNT_RESID, c->d_sc));
     P2G_TRY(pod2g_check_launch(c));
     // s0 = AMG(0; K, r0, r1, r2), convergence test at k = 0, rs0; JOINING -> ACTIVE
@@ -995,8 +1050,9 @@ int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, 
     int* d_slots = (int*)(c->d_mask + c->Bp);
     P2G_CUDA(cudaMemcpyAsync(c->d_mask, mask.data(), sizeof(int) * c->Bp, cudaMemcpyHostToDevice, c->stream));
     P2G_CUDA(cudaMemcpyAsync(d_slots, slots, sizeof(int) * nslots, cudaMemcpyHostToDevice, c->stream));
+    const ElemOp E = elem_op(c);
     LAUNCH_BS(k_resid, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, 1, c->d_mask, c->d_row_ptr, c->d_col_idx,
-                                                              c->d_vals32, c->d_xdf, c->d_bdf, c->d_rdf, c->d_part,
+                                                              c->d_vals32, E, c->d_xdf, c->d_bdf, c->d_rdf, c->d_part,
                                                               c->d_counters + CNT_RESID, c->d_sc));
     P2G_TRY(pod2g_check_launch(c));
     const long long tot = (long long)nslots * c->n;

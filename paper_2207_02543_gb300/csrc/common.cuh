@@ -20,6 +20,8 @@
 #define POD2G_THREADS 256      // threads per CTA of the row kernels
 #define POD2G_MAX_K 64         // largest supported number of POD modes
 #define POD2G_MAX_BP 256       // largest slot-lane count
+#define POD2G_ELEM_RE 8        // element positions per block row (elements adjacent to one node)
+#define POD2G_KREF_MAX 576     // reference-matrix entries, (npe * bs)^2 with npe * bs <= 24
 
 // ---------------------------------------------------------------------------- slot states
 enum SlotState : int { SLOT_IDLE = 0, SLOT_JOINING = 1, SLOT_ACTIVE = 2, SLOT_DONE = 3 };
@@ -66,6 +68,13 @@ struct pod2g_ctx {
     double* d_phi64 = nullptr;          // FP64 path
     float* d_phi32 = nullptr;           // mixed paths (BF16-rounded values for MIXED_BF16PHI)
     __nv_bfloat16* d_phi16 = nullptr;   // MIXED_BF16PHI: the basis as stored BF16
+
+    // element-factored operator (pod2g_create_elements; elem = 1)
+    int elem = 0, n_el = 0, npe = 0;
+    uint64_t* d_desc = nullptr;         // [nnzb] block descriptors (see ElemOp)
+    int32_t* d_rowel = nullptr;         // [nb][POD2G_ELEM_RE] adjacent elements, ascending, -1 padded
+    float* d_kref32 = nullptr;          // [npe*npe][bs*bs] FP32 reference sub-blocks
+    float* d_coef32 = nullptr;          // [n_el][Bp] FP32 coefficients, slot-interleaved
 
     // per-slot set-up results
     double* d_Lc = nullptr;             // [B][k][k] Cholesky factors (FP64)
@@ -248,6 +257,62 @@ __device__ __forceinline__ void last_cta_reset(unsigned* counter) {
     if (threadIdx.x == 0) *counter = 0u;
 }
 
+// ---------------------------------------------------------------------------- element-factored operator
+// K = sum_e c_e K_ref on the stored block pattern. One 64-bit descriptor per
+// stored block, shared by all slots: for each position p < 8 of the block row's
+// element list, bit 48 + p says that element holds the block, and bits 6p..6p+5
+// give its reference sub-block s = a * npe + b (a, b the local indices of the
+// row and column nodes). Bit 62: zero block (a fixed node's row or column); bit
+// 63: identity block (a fixed node's diagonal block).
+struct ElemOp {
+    const uint64_t* desc;     // [nnzb]
+    const int32_t* rowel;     // [nb][POD2G_ELEM_RE]
+    const float* coef;        // [n_el][Bp]
+    const float* kref;        // [npe*npe][bs*bs]
+    int nk;                   // floats in kref
+};
+
+static inline ElemOp elem_op(const pod2g_ctx* c) {
+    ElemOp E;
+    E.desc = c->d_desc;
+    E.rowel = c->d_rowel;
+    E.coef = c->d_coef32;
+    E.kref = c->d_kref32;
+    E.nk = c->npe * c->npe * c->bs * c->bs;
+    return E;
+}
+
+// The coefficients c_e of block row i's elements for one slot lane (0 where no element).
+__device__ __forceinline__ void elem_row_coefs(const ElemOp& E, int i, int lane, int Bp, float* ce) {
+    int el[POD2G_ELEM_RE];
+#pragma unroll
+    for (int p = 0; p < POD2G_ELEM_RE; ++p) el[p] = __ldg(E.rowel + (long long)i * POD2G_ELEM_RE + p);
+#pragma unroll
+    for (int p = 0; p < POD2G_ELEM_RE; ++p) ce[p] = el[p] >= 0 ? E.coef[(long long)el[p] * Bp + lane] : 0.f;
+}
+
+// Values of one block from its descriptor: the FP32 sum, in element order, of the
+// rounded products c_e * K_ref[s] (no contraction into FMA).
+template <int BS>
+__device__ __forceinline__ void elem_block_values(uint64_t d, const float* ce, const float* kref, float* v) {
+    if (d >> 62) {
+        const float dg = (d >> 63) ? 1.f : 0.f;
+#pragma unroll
+        for (int e = 0; e < BS * BS; ++e) v[e] = (e % (BS + 1) == 0) ? dg : 0.f;
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < BS * BS; ++e) v[e] = 0.f;
+#pragma unroll
+    for (int p = 0; p < POD2G_ELEM_RE; ++p) {
+        if ((d >> (48 + p)) & 1ull) {
+            const float* K = kref + (int)((d >> (6 * p)) & 63ull) * (BS * BS);
+#pragma unroll
+            for (int e = 0; e < BS * BS; ++e) v[e] = __fadd_rn(v[e], __fmul_rn(ce[p], K[e]));
+        }
+    }
+}
+
 // counters used by the last-CTA reductions (indices into ctx->d_counters)
 enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT_W = 5, CNT_N = 16 };
 
@@ -255,6 +320,14 @@ enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT
 int plain_solve(pod2g_ctx* c, int slot, const double* b_dev, const double* x0_dev, double tol, int maxit,
                 double* x_dev, int* iters, double* relres, int* status);
 int setup_values(pod2g_ctx* c, int slot, const double* vals_dev);
+int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev);
+// doubles describing one instance: matrix values, or element coefficients
+static inline size_t instance_len(const pod2g_ctx* c) {
+    return c->elem ? (size_t)c->n_el : (size_t)c->nnzb * c->bs * c->bs;
+}
+static inline int setup_instance(pod2g_ctx* c, int slot, const double* dev) {
+    return c->elem ? setup_coeffs(c, slot, dev) : setup_values(c, slot, dev);
+}
 int batched_load(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, const double* x0_dev,
                  const double* tol, const int* maxit);
 int batched_run(pod2g_ctx* c, const std::vector<int>& lanes);

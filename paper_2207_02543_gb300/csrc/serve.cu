@@ -23,9 +23,9 @@ static void finish(pod2g_ctx* c, ServeRequest* r, int status) {
 
 static int serve_plain_one(pod2g_ctx* c, ServeRequest* r) {
     const size_t n = c->n;
-    const size_t vb = sizeof(double) * (size_t)c->nnzb * c->bs * c->bs;
+    const size_t vb = sizeof(double) * instance_len(c);
     P2G_CUDA(cudaMemcpyAsync(c->d_stage, r->values.data(), vb, cudaMemcpyHostToDevice, c->stream));
-    P2G_TRY(setup_values(c, 0, c->d_stage));
+    P2G_TRY(setup_instance(c, 0, c->d_stage));
     int st = 0;
     P2G_CUDA(cudaMemcpyAsync(&st, c->d_setup_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));
@@ -46,7 +46,7 @@ static int serve_plain_one(pod2g_ctx* c, ServeRequest* r) {
 static void worker_main(pod2g_ctx* c) {
     cudaSetDevice(c->device);
     const size_t n = c->n;
-    const size_t vb = sizeof(double) * (size_t)c->nnzb * c->bs * c->bs;
+    const size_t vb = sizeof(double) * instance_len(c);
     std::vector<ServeRequest*> lane_req(c->B, nullptr);
     int fatal = POD2G_OK;
     while (true) {
@@ -94,7 +94,7 @@ static void worker_main(pod2g_ctx* c) {
                 ServeRequest* r = joining[i];
                 int b = jl[i];
                 if (cudaMemcpyAsync(c->d_stage, r->values.data(), vb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-                    setup_values(c, b, c->d_stage) != POD2G_OK) {
+                    setup_instance(c, b, c->d_stage) != POD2G_OK) {
                     fatal = POD2G_CUDA_ERROR;
                     break;
                 }
@@ -188,7 +188,7 @@ int pod2g_submit(pod2g_t c, const double* values, const double* b, const double*
                  uint64_t* ticket) {
     if (!c || !values || !b || !ticket || !(tol >= 0.0) || maxit < 0) return POD2G_INVALID_ARG;
     const size_t n = c->n;
-    const size_t nv = (size_t)c->nnzb * c->bs * c->bs;
+    const size_t nv = instance_len(c);
     {
         std::lock_guard<std::mutex> g(c->mu);
         if (!c->serving) return POD2G_INVALID_ARG;

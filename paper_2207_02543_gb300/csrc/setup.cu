@@ -82,6 +82,35 @@ __global__ void k_w_f64(const int32_t* __restrict__ row_ptr, const int32_t* __re
     W[d * kp + m] = acc;
 }
 
+// Element coefficients (FP64, one instance) -> the slot's lane of the FP32
+// interleaved array; status NONFINITE on a NaN or Inf.
+__global__ void k_coef_convert(const double* __restrict__ c64, float* __restrict__ coef32, int n_el, int Bp,
+                               int slot, int* __restrict__ status) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += gridDim.x * blockDim.x) {
+        const double v = c64[e];
+        if (!isfinite(v)) atomicExch(status, (int)POD2G_NONFINITE);
+        coef32[(long long)e * Bp + slot] = __double2float_rn(v);
+    }
+}
+
+// The FP32 values of one slot's element operator, contiguous [nnzb][bs*bs]
+// (one thread per block row), from the same block-value routine the solver's
+// row kernels use.
+template <int BS>
+__global__ void k_elem_stage(ElemOp E, const int32_t* __restrict__ row_ptr, int nb, int Bp, int slot,
+                             float* __restrict__ stage32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+        float ce[POD2G_ELEM_RE];
+        elem_row_coefs(E, i, slot, Bp, ce);
+        for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
+            float v[BS * BS];
+            elem_block_values<BS>(E.desc[blk], ce, E.kref, v);
+#pragma unroll
+            for (int e = 0; e < BS * BS; ++e) stage32[(long long)blk * BS * BS + e] = v[e];
+        }
+    }
+}
+
 #define AC_TILE 32
 
 // Contraction K_c = Phi^T W (k x k), split over CTAs along the n rows; the last
@@ -194,6 +223,46 @@ __global__ void k_ac(const void* __restrict__ phi_v, const void* __restrict__ W_
 
 }  // namespace
 
+// Mixed paths: D^-1, K Phi, K_c and its Cholesky factor from the slot's FP32 values in d_stage32.
+static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
+    const int T = POD2G_THREADS;
+    const int n = c->n;
+    const float* stage32 = c->d_stage32;
+    double* L = c->d_Lc + (size_t)slot * c->k * c->k;
+    k_dinv<float><<<ceil_div(n, T), T, 0, c->stream>>>(stage32, c->d_diag_blk, c->nb, c->bs, nullptr, c->d_dinv32,
+                                                        c->Bp, slot, st);
+    P2G_TRY(pod2g_check_launch(c));
+    if (c->k > 0) {
+        long long tw = (long long)n * c->kp;
+        k_w_df<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, stage32, c->d_phi32, c->nb, c->bs,
+                                                     c->kp, (float2*)c->d_W);
+        P2G_TRY(pod2g_check_launch(c));
+        int ga = std::max(1, std::min(2 * c->num_sms, ceil_div(n, 256)));
+        k_ac<true><<<ga, T, 0, c->stream>>>(c->d_phi32, c->d_W, n, c->k, c->kp, c->d_ac_part,
+                                            c->d_counters + CNT_AC, c->d_Ac, L, st);
+        P2G_TRY(pod2g_check_launch(c));
+    }
+    return POD2G_OK;
+}
+
+// Element contexts: coefficients (FP64, device) -> the slot's FP32 lane, the FP32
+// operator values of that slot, then the common set-up.
+int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev) {
+    const int T = POD2G_THREADS;
+    P2G_CUDA(cudaMemsetAsync(c->d_setup_status + slot, 0, sizeof(int), c->stream));
+    int* st = c->d_setup_status + slot;
+    k_coef_convert<<<std::min(ceil_div(c->n_el, T), 8 * c->num_sms), T, 0, c->stream>>>(
+        coef_dev, c->d_coef32, c->n_el, c->Bp, slot, st);
+    P2G_TRY(pod2g_check_launch(c));
+    const ElemOp E = elem_op(c);
+    const int g = std::min(ceil_div(c->nb, T), 8 * c->num_sms);
+    if (c->bs == 1) k_elem_stage<1><<<g, T, 0, c->stream>>>(E, c->d_row_ptr, c->nb, c->Bp, slot, c->d_stage32);
+    else if (c->bs == 2) k_elem_stage<2><<<g, T, 0, c->stream>>>(E, c->d_row_ptr, c->nb, c->Bp, slot, c->d_stage32);
+    else k_elem_stage<3><<<g, T, 0, c->stream>>>(E, c->d_row_ptr, c->nb, c->Bp, slot, c->d_stage32);
+    P2G_TRY(pod2g_check_launch(c));
+    return setup_from_stage32(c, slot, st);
+}
+
 int setup_values(pod2g_ctx* c, int slot, const double* vals_dev) {
     const long long total = (long long)c->nnzb * c->bs * c->bs;
     const int T = POD2G_THREADS;
@@ -220,23 +289,10 @@ int setup_values(pod2g_ctx* c, int slot, const double* vals_dev) {
             P2G_TRY(pod2g_check_launch(c));
         }
     } else {
-        float* stage32 = c->d_stage32;
         int g = std::min(ceil_div(total, T), 8 * c->num_sms);
-        k_convert_values<<<g, T, 0, c->stream>>>(vals_dev, stage32, c->d_vals32, total, c->Bp, slot);
+        k_convert_values<<<g, T, 0, c->stream>>>(vals_dev, c->d_stage32, c->d_vals32, total, c->Bp, slot);
         P2G_TRY(pod2g_check_launch(c));
-        k_dinv<float><<<ceil_div(n, T), T, 0, c->stream>>>(stage32, diag_blk, c->nb, c->bs, nullptr, c->d_dinv32,
-                                                            c->Bp, slot, st);
-        P2G_TRY(pod2g_check_launch(c));
-        if (c->k > 0) {
-            long long tw = (long long)n * c->kp;
-            k_w_df<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, stage32, c->d_phi32, c->nb,
-                                                         c->bs, c->kp, (float2*)c->d_W);
-            P2G_TRY(pod2g_check_launch(c));
-            int ga = std::max(1, std::min(2 * c->num_sms, ceil_div(n, 256)));
-            k_ac<true><<<ga, T, 0, c->stream>>>(c->d_phi32, c->d_W, n, c->k, c->kp, c->d_ac_part,
-                                                c->d_counters + CNT_AC, c->d_Ac, L, st);
-            P2G_TRY(pod2g_check_launch(c));
-        }
+        P2G_TRY(setup_from_stage32(c, slot, st));
     }
     return POD2G_OK;
 }
