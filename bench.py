@@ -280,6 +280,13 @@ def gb300_arm(args):
         assert rc == pkg.OK, (pkg.strerror(rc), status)
         return iters, rel
 
+    tuning = None
+    if not args.no_autotune:
+        # launch shapes picked by timing candidates on this workload (outside the timed region)
+        st, sts = set_batch(slots, vals)
+        assert st == pkg.OK, pkg.strerror(st)
+        st, tuning = s.autotune(slots, b_dev, iters=16)
+        assert st == pkg.OK, pkg.strerror(st)
     torch.cuda.synchronize()
     for _ in range(max(args.warmup, 0)):
         iters, rel = step()
@@ -398,7 +405,7 @@ def gb300_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
             "config": {"workload": workload_desc(wl, B, tol), "method": method_name(args.method),
-                       "operator": args.operator,
+                       "operator": args.operator, "tuning": tuning,
                        "batch": B, "n": P.n, "nnzb": P.nnzb, "k": wl.spec.k, "parallelism": f"replicas{world}",
                        "l2": (f"inputs larger than L2 ({vals.numel() * 8 / 1e9:.2f} GB FP64 "
                               f"{'coefficients' if elements else 'values'} per step; per-iteration working set "
@@ -465,6 +472,7 @@ def main():
                     help="pcg: Algorithm 3; stationary: the two-grid cycle of Algorithm 2 iterated on its own")
     ap.add_argument("--operator", default="assembled", choices=["assembled", "elements"],
                     help="instances as assembled block values, or as element coefficients (element-factored K)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--tol", type=float, default=TOL)
     ap.add_argument("--maxit", type=int, default=MAXIT)
     args = ap.parse_args()

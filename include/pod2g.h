@@ -267,6 +267,29 @@ int pod2g_solve_noalloc(int32_t n_brows, int32_t bs, int32_t nnzb, const int32_t
                         const pod2g_opts* opts, const double* b_dev, const double* x0_dev, double tol,
                         int maxit, double* x_dev, int* iters, double* relres, int* status, void* stream);
 
+/* ---- Launch shapes of the batched (mixed-precision) path: CTAs per grid of each
+ * kernel group. A shape changes only the grouping of partial sums, so results are
+ * deterministic for a given shape and differ between shapes at rounding level. */
+typedef struct {
+    int32_t grid_rows;      /* sparse row kernels (SpMV, smoothers, residual): multiple of 8, 8..8*SMs */
+    int32_t grid_restrict;  /* restriction Phi^T r: multiple of 8, 8..4*SMs */
+    int32_t grid_prol;      /* prolongation: 1..8*SMs */
+    int32_t grid_vec;       /* vector updates (p; x and r): 1..8*SMs */
+} pod2g_tuning;
+
+/* Current shape (mixed contexts; FP64 contexts return POD2G_INVALID_ARG). */
+int pod2g_get_tuning(pod2g_t ctx, pod2g_tuning* out);
+/* Set a shape; POD2G_INVALID_ARG if a field is out of range or the context is serving. */
+int pod2g_set_tuning(pod2g_t ctx, const pod2g_tuning* t);
+/* Autotuner: for five candidate shapes, solve the given set-up slots with right-hand
+ * sides b_dev (nslots consecutive vectors of n doubles, device) for `iters`
+ * iterations (rounded up to whole graph launches), timing each kernel with CUDA
+ * events, and keep per kernel group the fastest candidate. The slots are left idle
+ * (their set-up stays valid). *out (may be NULL) receives the chosen shape. Not
+ * while serving. */
+int pod2g_autotune(pod2g_t ctx, int nslots, const int* slots, const double* b_dev, int iters,
+                   pod2g_tuning* out);
+
 /* Static message for a status code. Never NULL. */
 const char* pod2g_strerror(int status);
 

@@ -24,7 +24,7 @@ EXPORTS = [
     "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
     "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_kernel_timing", "pod2g_kernel_times",
     "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc", "pod2g_device_bytes", "pod2g_create_elements",
-    "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
+    "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev", "pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune",
 ]
 NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
 TOO_LARGE = 11
@@ -39,6 +39,11 @@ class Pattern(C.Structure):
 class Elements(C.Structure):
     _fields_ = [("n_elems", C.c_int32), ("npe", C.c_int32), ("conn", C.POINTER(C.c_int32)),
                 ("k_ref", C.POINTER(C.c_double)), ("fixed", C.POINTER(C.c_uint8))]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("grid_rows", C.c_int32), ("grid_restrict", C.c_int32), ("grid_prol", C.c_int32),
+                ("grid_vec", C.c_int32)]
 
 
 class Opts(C.Structure):
@@ -67,6 +72,9 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_create_elements.argtypes = [C.POINTER(Pattern), C.POINTER(Elements), DP, I, C.POINTER(Opts),
                                           C.POINTER(P)]
     lib.pod2g_set_coeffs.argtypes = [P, I, P, I]
+    lib.pod2g_get_tuning.argtypes = [P, C.POINTER(Tuning)]
+    lib.pod2g_set_tuning.argtypes = [P, C.POINTER(Tuning)]
+    lib.pod2g_autotune.argtypes = [P, I, IP, P, I, C.POINTER(Tuning)]
     lib.pod2g_set_coeffs_batch_dev.argtypes = [P, I, IP, P, IP]
     lib.pod2g_set_values.argtypes = [P, I, P, I]
     lib.pod2g_set_values_batch_dev.argtypes = [P, I, IP, P, IP]
@@ -93,7 +101,7 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_destroy.restype = None
     lib.pod2g_strerror.argtypes = [I]
     lib.pod2g_strerror.restype = C.c_char_p
-    for name in ("pod2g_create", "pod2g_create_elements", "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
+    for name in ("pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune", "pod2g_create", "pod2g_create_elements", "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
                  "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
                  "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
                  "pod2g_serve_stop", "pod2g_info"):
@@ -215,6 +223,30 @@ class Solver:
                 return INVALID_ARG
             st = self._lib.pod2g_set_values(self.h, slot, v.ctypes.data_as(C.c_void_p), 0)
         return st
+
+    # -------------------------------------------------------------- launch shapes
+    def get_tuning(self):
+        t = Tuning()
+        st = self._lib.pod2g_get_tuning(self.h, C.byref(t))
+        if st != OK:
+            raise Pod2gError(st, "pod2g_get_tuning")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    def set_tuning(self, **shape) -> int:
+        cur = self.get_tuning()
+        cur.update(shape)
+        return self._lib.pod2g_set_tuning(self.h, C.byref(Tuning(**cur)))
+
+    def autotune(self, slots, b_dev, iters=16):
+        """Time candidate launch shapes on the given set-up slots (b_dev: CUDA float64 tensor
+        [len(slots), n]) and keep the fastest per kernel group. Returns (status, shape)."""
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        if b_dev.numel() != len(slots) * self.n:
+            return INVALID_ARG, None
+        t = Tuning()
+        st = self._lib.pod2g_autotune(self.h, len(slots), slots.ctypes.data_as(C.POINTER(C.c_int)),
+                                      C.c_void_p(b_dev.data_ptr()), iters, C.byref(t))
+        return st, ({f: getattr(t, f) for f, _ in Tuning._fields_} if st == OK else None)
 
     def set_coeffs(self, slot: int, coeffs) -> int:
         """Element contexts: coeffs, numpy float64 (host) or a CUDA float64 tensor, n_elems entries."""

@@ -414,6 +414,29 @@ int pod2g_kernel_timing(pod2g_t c, int on) {
     return batched_set_timing(c, on);
 }
 
+static int check_slots(pod2g_ctx* c, int nslots, const int* slots);
+
+int pod2g_get_tuning(pod2g_t c, pod2g_tuning* out) {
+    if (!c || !out || c->precision == POD2G_FP64) return POD2G_INVALID_ARG;
+    out->grid_rows = c->grid_rows;
+    out->grid_restrict = c->grid_restrict;
+    out->grid_prol = c->grid_prol;
+    out->grid_vec = c->grid_vec;
+    return POD2G_OK;
+}
+
+int pod2g_set_tuning(pod2g_t c, const pod2g_tuning* t) {
+    if (!c || !t || c->precision == POD2G_FP64 || c->serving) return POD2G_INVALID_ARG;
+    return batched_set_tuning(c, t);
+}
+
+int pod2g_autotune(pod2g_t c, int nslots, const int* slots, const double* b_dev, int iters, pod2g_tuning* out) {
+    if (!c || !b_dev || iters < 1 || c->precision == POD2G_FP64 || c->serving) return POD2G_INVALID_ARG;
+    P2G_TRY(check_slots(c, nslots, slots));
+    P2G_TRY(batched_autotune(c, nslots, slots, b_dev, iters));
+    return out ? pod2g_get_tuning(c, out) : POD2G_OK;
+}
+
 int pod2g_kernel_times(pod2g_t c, double* ms, int64_t* launches) {
     if (!c) return POD2G_INVALID_ARG;
     for (int j = 0; j < 8; ++j) {

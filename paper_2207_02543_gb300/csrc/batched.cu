@@ -796,7 +796,7 @@ static size_t restrict_smem(int Bp, int kp) {
     const int teams = POD2G_THREADS / ((Bp / lb) * (kp / 8));
     return (size_t)Bp * kp * sizeof(double) + (size_t)teams * Bp * kp * sizeof(float);
 }
-static int restrict_grid(pod2g_ctx* c) { return batched_grid(c->num_sms, (long long)2 * c->num_sms * POD2G_THREADS); }
+static int restrict_grid(pod2g_ctx* c) { return c->grid_restrict; }
 
 #define LB_LIST(X, KP) X(KP, 1) X(KP, 2) X(KP, 4) X(KP, 8)
 static void launch_restrict(pod2g_ctx* c, Dims D, int want) {
@@ -816,7 +816,7 @@ static void launch_restrict(pod2g_ctx* c, Dims D, int want) {
 static void launch_prol(pod2g_ctx* c, Dims D, int want) {
     const size_t sm = sizeof(float) * c->Bp * (c->kp + 1);
     const long long n = c->n;
-    const int gp = std::max(1, std::min(ceil_div(n * c->Bp, POD2G_THREADS), 8 * c->num_sms));
+    const int gp = std::max(1, std::min(ceil_div(n * c->Bp, POD2G_THREADS), c->grid_prol));
 #define CASE_KP(KP_)                                                                                              \
     case KP_:                                                                                                     \
         if (c->pre)                                                                                               \
@@ -882,7 +882,7 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
 // one PCG iteration (Algorithm 3 loop body) for ACTIVE lanes
 static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     const long long total = (long long)c->n * c->Bp;
-    const int ge = elementwise_grid(c, total);
+    const int ge = std::max(1, std::min(ceil_div(total, POD2G_THREADS), c->grid_vec));
     if (c->cap_ev) P2G_CUDA(cudaEventRecordWithFlags(c->cap_ev[c->cap_idx++], c->stream, cudaEventRecordExternal));
     k_p<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_s32, c->d_pdf, c->d_sc, total);
     P2G_TRY(mark(c));
@@ -902,6 +902,9 @@ int batched_alloc(pod2g_ctx* c) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c->num_sms = sms > 0 ? sms : 152;
     c->grid_rows = batched_grid(c->num_sms, (long long)c->nb * c->Bp);
+    c->grid_restrict = batched_grid(c->num_sms, (long long)2 * c->num_sms * POD2G_THREADS);
+    c->grid_prol = 8 * c->num_sms;
+    c->grid_vec = 8 * c->num_sms;
     if (c->precision != POD2G_FP64 && c->kp > 0) {
         const int sm_r = (int)restrict_smem(c->Bp, c->kp);
         const int lb = restrict_lb(c->Bp, c->kp);
@@ -1067,5 +1070,80 @@ int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, 
         if (relres) relres[i] = s.relres;
         if (status) status[i] = s.state == SLOT_DONE ? s.result : POD2G_NOT_CONVERGED;
     }
+    return POD2G_OK;
+}
+
+// ---------------------------------------------------------------------------- launch shapes
+int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
+    const int sms = c->num_sms;
+    if (t->grid_rows < CLUSTER || t->grid_rows % CLUSTER || t->grid_rows > 8 * sms) return POD2G_INVALID_ARG;
+    if (t->grid_restrict < CLUSTER || t->grid_restrict % CLUSTER || t->grid_restrict > 4 * sms) return POD2G_INVALID_ARG;
+    if (t->grid_prol < 1 || t->grid_prol > 8 * sms || t->grid_vec < 1 || t->grid_vec > 8 * sms) return POD2G_INVALID_ARG;
+    c->grid_rows = t->grid_rows;
+    c->grid_restrict = t->grid_restrict;
+    c->grid_prol = t->grid_prol;
+    c->grid_vec = t->grid_vec;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    return POD2G_OK;
+}
+
+// Autotuner: run `iters` iterations of the given (set-up) slots for each of a few
+// candidate launch shapes, timing every kernel with CUDA events inside the graph,
+// and keep per kernel group the fastest shape: row kernels (k_spmv + k_smooth1 +
+// k_post), restriction, prolongation, vector updates (k_p + k_upd). The slots are
+// left idle. The result depends on measured times; a given shape gives
+// deterministic results, and shapes differ only in the summation order of partials.
+int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, int iters) {
+    const int sms = c->num_sms;
+    const int NC = 5;
+    auto r8 = [&](int g, int cap) { return std::max(CLUSTER, std::min(cap, g) / CLUSTER * CLUSTER); };
+    const int need_rows = batched_grid(sms, (long long)c->nb * c->Bp);
+    const int need_vec = std::max(1, ceil_div((long long)c->n * c->Bp, POD2G_THREADS));
+    const int row_f[NC] = {3, 4, 5, 6, 8}, res_f[NC] = {1, 2, 3, 4, 4}, vec_f[NC] = {2, 3, 4, 6, 8};
+    pod2g_tuning cand[NC];
+    for (int j = 0; j < NC; ++j) {
+        cand[j].grid_rows = r8(row_f[j] * sms, need_rows);
+        cand[j].grid_restrict = r8(res_f[j] * sms, 4 * sms);
+        cand[j].grid_prol = std::min(vec_f[j] * sms, need_vec);
+        cand[j].grid_vec = std::min(vec_f[j] * sms, need_vec);
+    }
+    const bool timing0 = c->timing;
+    std::vector<double> tol(nslots, 0.0);
+    std::vector<int> maxit(nslots, iters + 16 * c->chunk);
+    std::vector<int> lanes(slots, slots + nslots);
+    double t_rows[NC], t_res[NC], t_prol[NC], t_vec[NC];
+    for (int j = 0; j < NC; ++j) {
+        P2G_TRY(batched_set_tuning(c, &cand[j]));
+        P2G_TRY(batched_set_timing(c, 1));
+        P2G_TRY(batched_load(c, nslots, slots, b_dev, nullptr, tol.data(), maxit.data()));
+        for (int it = 0; it < iters; it += c->chunk) P2G_TRY(batched_chunk(c));
+        auto per = [&](int k) { return c->kt_n[k] ? c->kt_ms[k] / (double)c->kt_n[k] : 0.0; };
+        t_vec[j] = per(0) + per(2);               // k_p, k_upd
+        t_rows[j] = per(1) + per(3) + per(7);     // k_spmv, k_smooth1, k_post
+        t_res[j] = per(4);                        // k_restrict
+        t_prol[j] = per(6);                       // k_prol
+    }
+    auto best = [&](const double* t) {
+        int b = 0;
+        for (int j = 1; j < NC; ++j)
+            if (t[j] < t[b]) b = j;
+        return b;
+    };
+    pod2g_tuning pick;
+    pick.grid_rows = cand[best(t_rows)].grid_rows;
+    pick.grid_restrict = cand[best(t_res)].grid_restrict;
+    pick.grid_prol = cand[best(t_prol)].grid_prol;
+    pick.grid_vec = cand[best(t_vec)].grid_vec;
+    P2G_TRY(batched_set_tuning(c, &pick));
+    P2G_TRY(batched_set_timing(c, timing0 ? 1 : 0));
+    // leave the slots idle
+    P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
+    P2G_CUDA(cudaStreamSynchronize(c->stream));
+    for (int b : lanes) c->h_sc[b].state = SLOT_IDLE;
+    P2G_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyHostToDevice, c->stream));
+    P2G_CUDA(cudaStreamSynchronize(c->stream));
     return POD2G_OK;
 }

@@ -119,7 +119,10 @@ struct pod2g_ctx {
     int* d_mask = nullptr;              // [2 Bp] lane mask and slot list for load / finalize
     double* d_iob = nullptr;            // [B][n] staging of right-hand sides (host-buffer entry points)
     double* d_iox = nullptr;            // [B][n] staging of x0 / x
-    int grid_rows = 0;                  // CTAs of the row kernels
+    int grid_rows = 0;                  // CTAs of the row kernels (multiple of the cluster size 8)
+    int grid_restrict = 0;              // CTAs of the restriction (multiple of 8)
+    int grid_prol = 0;                  // CTAs of the prolongation
+    int grid_vec = 0;                   // CTAs of the vector updates (p, x/r)
     cudaGraphExec_t graph_exec = nullptr;
     // per-kernel timing (event-record nodes around each kernel of the captured iterations)
     bool timing = false;
@@ -337,5 +340,7 @@ int batched_grid(int num_sms, long long items);
 int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, int* iters, double* relres,
                      int* status);
 int batched_alloc(pod2g_ctx* c);
+int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t);
+int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, int iters);
 void batched_free(pod2g_ctx* c);
 int dev_alloc(pod2g_ctx* c, void** p, size_t bytes);

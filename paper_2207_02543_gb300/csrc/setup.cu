@@ -36,7 +36,7 @@ __global__ void k_dinv(const V* __restrict__ vals, const int32_t* __restrict__ d
     int i = d / bs, rr = d - i * bs;
     double a = (double)vals[(long long)diag_blk[i] * bs * bs + rr * bs + rr];
     if (!(a > 0.0) || !isfinite(a)) {
-        atomicExch(status, (int)POD2G_NOT_SPD);
+        atomicCAS(status, (int)POD2G_OK, (int)POD2G_NOT_SPD);
         a = 1.0;
     }
     if (dinv64) dinv64[d] = 1.0 / a;
@@ -88,7 +88,7 @@ __global__ void k_coef_convert(const double* __restrict__ c64, float* __restrict
                                int slot, int* __restrict__ status) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += gridDim.x * blockDim.x) {
         const double v = c64[e];
-        if (!isfinite(v)) atomicExch(status, (int)POD2G_NONFINITE);
+        if (!isfinite(v)) atomicCAS(status, (int)POD2G_OK, (int)POD2G_NONFINITE);
         coef32[(long long)e * Bp + slot] = __double2float_rn(v);
     }
 }
@@ -217,7 +217,7 @@ __global__ void k_ac(const void* __restrict__ phi_v, const void* __restrict__ W_
         int i = pr / k, j = pr - i * k;
         if (j > i) Lout[pr] = 0.0;
     }
-    if (threadIdx.x == 0 && fail) atomicExch(status, (int)POD2G_NOT_SPD);
+    if (threadIdx.x == 0 && fail) atomicCAS(status, (int)POD2G_OK, (int)POD2G_NOT_SPD);
     last_cta_reset(counter);
 }
 

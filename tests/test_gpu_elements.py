@@ -110,12 +110,17 @@ def test_element_serving_matches_batch(pkg):
     m = 6
     coefs = [wl.coef(xi) for xi in wl.query_thetas(m)]
     Bm = wl.rhs(m)
-    se = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, elements=_elements(P), max_batch=m, omega=wl.spec.omega,
+    # same slot count as the serving context (the per-slot summation order depends on
+    # the lane stride, i.e. on max_batch, and on nothing else)
+    se = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, elements=_elements(P), max_batch=3, omega=wl.spec.omega,
                     chunk=4)
-    for i in range(m):
-        assert se.set_coeffs(i, coefs[i]) == pkg.OK
-    X, it, rel, st, rc = se.solve_batch(list(range(m)), Bm, tol=TOL, maxit=3000)
-    assert rc == pkg.OK
+    X, it = np.zeros((m, P.n)), np.zeros(m, dtype=int)
+    for g in range(0, m, 3):
+        for i in range(3):
+            assert se.set_coeffs(i, coefs[g + i]) == pkg.OK
+        Xg, itg, rel, st, rc = se.solve_batch([0, 1, 2], Bm[g:g + 3], tol=TOL, maxit=3000)
+        assert rc == pkg.OK
+        X[g:g + 3], it[g:g + 3] = Xg, itg
     srv = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, elements=_elements(P), max_batch=3, omega=wl.spec.omega,
                      chunk=4)
     srv.serve_start(max_queue=16)
