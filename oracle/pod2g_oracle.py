@@ -16,6 +16,8 @@ parametrized systems"), in the paper's order and notation:
   * pod2g_preconditioner     s = AMG(0; K, r, r1, r2), Algorithm 3
   * damped_jacobi            the relaxation scheme G (damped Jacobi; the paper
                              analyses Gauss-Seidel, eq. GaussSeidel)
+  * gauss_seidel             pointwise Gauss-Seidel, eq. GaussSeidel, in a multicolour
+    multicolour_groups       order (forward before, backward after the correction)
   * pod_method_of_snapshots  Section 3.3 steps 1-2, eq. PODrelationEigenvectors
   * coarse_operator          K_r = Phi_r^T K Phi_r, eq. POD_ROM
   * rom_solution             u = Phi_r K_r^{-1} Phi_r^T f, Section 3.3 steps 3-4
@@ -128,18 +130,63 @@ def damped_jacobi(K, Dinv, omega, f, u, sweeps):
     return u
 
 
-def two_grid_cycle(K, f, u, Phi, L_c, Dinv, omega, r1, r2, trace=None):
+def multicolour_groups(row_ptr, col_idx, bs):
+    """Independent dof groups for Gauss-Seidel: nodes (block rows) are coloured
+    greedily in index order, each taking the smallest colour that no neighbour of a
+    lower index holds, so nodes of one colour share no stored block. Group (c, a)
+    holds component a of every node of colour c; the dofs of one group do not couple,
+    so a sweep over the groups in order (c = 0, 1, ..; a = 0..bs-1 within c) is a
+    pointwise Gauss-Seidel sweep. Returns the list of dof index arrays in sweep order."""
+    nb = len(row_ptr) - 1
+    colour = np.full(nb, -1, dtype=np.int64)
+    for i in range(nb):
+        taken = {int(colour[j]) for j in col_idx[row_ptr[i]:row_ptr[i + 1]] if j < i}
+        c = 0
+        while c in taken:
+            c += 1
+        colour[i] = c
+    groups = []
+    for c in range(int(colour.max()) + 1):
+        nodes = np.nonzero(colour == c)[0]
+        for a in range(bs):
+            groups.append(nodes * bs + a)
+    return groups
+
+
+def gauss_seidel(K, Kdiag, f, u, groups, sweeps, reverse=False):
+    """`sweeps` pointwise Gauss-Seidel sweeps u_d <- u_d + (f - K u)_d / K_dd over the
+    dofs in the order of `groups` (reversed for the backward sweep): the relaxation
+    scheme of eq. GaussSeidel (Section 2.2). Each group is updated at once, which is
+    exact because its dofs do not couple."""
+    order = groups[::-1] if reverse else groups
+    u = np.array(u, dtype=np.float64)
+    for _ in range(sweeps):
+        for g in order:
+            u[g] = u[g] + (f[g] - K[g] @ u) / Kdiag[g]
+    return u
+
+
+def two_grid_cycle(K, f, u, Phi, L_c, Dinv, omega, r1, r2, trace=None, groups=None):
     """One cycle of Algorithm 2 with prolongation P = Phi (Section 3.3):
     pre-relax r1 times, residual, restrict and solve K_c e_c = Phi^T r, prolong,
-    correct, post-relax r2 times."""
-    u = damped_jacobi(K, Dinv, omega, f, u, r1)          # pre-relaxation
+    correct, post-relax r2 times. Relaxation: damped Jacobi, or with `groups`
+    forward Gauss-Seidel before and backward Gauss-Seidel after the coarse
+    correction (the symmetric pair, so that the cycle from zero is a symmetric
+    preconditioner)."""
+    if groups is None:
+        u = damped_jacobi(K, Dinv, omega, f, u, r1)      # pre-relaxation
+    else:
+        u = gauss_seidel(K, 1.0 / Dinv, f, u, groups, r1)
     r = f - K @ u                                         # residual update
     e_c = cholesky_solve(L_c, Phi.T @ r)                  # K_c e_c = P^T r
     e = Phi @ e_c                                         # prolongation
     u = u + e                                             # correction
     if trace is not None:
         trace["after_correction"] = u.copy()
-    u = damped_jacobi(K, Dinv, omega, f, u, r2)          # post-relaxation
+    if groups is None:
+        u = damped_jacobi(K, Dinv, omega, f, u, r2)      # post-relaxation
+    else:
+        u = gauss_seidel(K, 1.0 / Dinv, f, u, groups, r2, reverse=True)
     return u
 
 
@@ -152,19 +199,21 @@ class Pod2gSetup:
     omega: float
     r1: int = 1
     r2: int = 1
+    groups: list | None = None     # Gauss-Seidel sweep groups (None: damped Jacobi)
 
 
-def pod2g_setup(K, Phi, omega, r1=1, r2=1) -> Pod2gSetup:
+def pod2g_setup(K, Phi, omega, r1=1, r2=1, groups=None) -> Pod2gSetup:
     Dinv = jacobi_inverse_diagonal(K)
     L_c = cholesky(coarse_operator(K, Phi)) if Phi.shape[1] > 0 else np.zeros((0, 0))
-    return Pod2gSetup(Phi=np.asarray(Phi, dtype=np.float64), Dinv=Dinv, L_c=L_c, omega=omega, r1=r1, r2=r2)
+    return Pod2gSetup(Phi=np.asarray(Phi, dtype=np.float64), Dinv=Dinv, L_c=L_c, omega=omega, r1=r1, r2=r2,
+                      groups=groups)
 
 
 def pod2g_preconditioner(K, setup: Pod2gSetup):
     """r -> AMG(0; K, r, r1, r2): one two-grid cycle from a zero initial guess (Algorithm 3)."""
     def apply(r):
         return two_grid_cycle(K, r, np.zeros_like(r), setup.Phi, setup.L_c, setup.Dinv,
-                              setup.omega, setup.r1, setup.r2)
+                              setup.omega, setup.r1, setup.r2, groups=setup.groups)
     return apply
 
 
@@ -240,10 +289,10 @@ def pcg(K, f, u0, apply_Tinv, tol, maxit, beta="fr", record=False) -> PCGResult:
     return PCGResult(u, k, status, true_rel, hist, recs)
 
 
-def pod2g_pcg(K, f, u0, Phi, omega, tol, maxit, r1=1, r2=1, beta="fr", record=False) -> PCGResult:
+def pod2g_pcg(K, f, u0, Phi, omega, tol, maxit, r1=1, r2=1, beta="fr", record=False, groups=None) -> PCGResult:
     """POD-2G-preconditioned CG: Algorithm 3 with the two-grid cycle of Algorithm 2, P = Phi_r."""
     try:
-        st = pod2g_setup(K, Phi, omega, r1, r2)
+        st = pod2g_setup(K, Phi, omega, r1, r2, groups)
     except np.linalg.LinAlgError:
         return PCGResult(np.zeros(K.shape[0]) if u0 is None else np.array(u0, float), 0, NOT_SPD, np.nan)
     return pcg(K, f, u0, pod2g_preconditioner(K, st), tol, maxit, beta=beta, record=record)
@@ -254,16 +303,27 @@ def jacobi_pcg(K, f, u0, tol, maxit, record=False) -> PCGResult:
 
 
 # ----------------------------------------------------------------------------- operators (dense, tiny cases)
-def two_grid_error_operator(K, Phi, Dinv, omega, r1=1, r2=1) -> np.ndarray:
-    """Dense e -> M^{r2} C M^{r1} e with M = I - omega D^{-1} K and
-    C = I - Phi (Phi^T K Phi)^{-1} Phi^T K (eq. AMGerror, eq. FinalScheme)."""
+def two_grid_error_operator(K, Phi, Dinv, omega, r1=1, r2=1, order=None) -> np.ndarray:
+    """Dense e -> M2^{r2} C M1^{r1} e with C = I - Phi (Phi^T K Phi)^{-1} Phi^T K
+    (eq. AMGerror, eq. FinalScheme) and M1 = M2 = I - omega D^{-1} K (damped Jacobi),
+    or, given a dof `order`, the Gauss-Seidel splittings of the permuted matrix:
+    M1 = I - (D + L)^{-1} K (forward), M2 = I - (D + U)^{-1} K (backward), L / U the
+    strictly lower / upper triangles of K in that order (eq. GaussSeidel)."""
     Kd = K.toarray() if hasattr(K, "toarray") else np.asarray(K)
     n = Kd.shape[0]
     I = np.eye(n)
-    M = I - omega * Dinv[:, None] * Kd
+    if order is None:
+        M1 = M2 = I - omega * Dinv[:, None] * Kd
+    else:
+        Pm = np.eye(n)[order]                   # row t of Pm picks dof order[t]
+        Kp = Pm @ Kd @ Pm.T
+        lower = np.tril(Kp)
+        upper = np.triu(Kp)
+        M1 = I - Pm.T @ np.linalg.solve(lower, Kp) @ Pm
+        M2 = I - Pm.T @ np.linalg.solve(upper, Kp) @ Pm
     Kc = Phi.T @ Kd @ Phi
     C = I - Phi @ np.linalg.solve(Kc, Phi.T @ Kd)
-    return np.linalg.matrix_power(M, r2) @ C @ np.linalg.matrix_power(M, r1)
+    return np.linalg.matrix_power(M2, r2) @ C @ np.linalg.matrix_power(M1, r1)
 
 
 def spectral_radius_estimate(K, Dinv, steps=30, seed=0) -> float:
@@ -280,7 +340,7 @@ def spectral_radius_estimate(K, Dinv, steps=30, seed=0) -> float:
 
 
 # ----------------------------------------------------------------------------- Algorithm 2 as a solver
-def pod2g_stationary(K, f, u0, Phi, omega, tol, maxit, r1=1, r2=1) -> PCGResult:
+def pod2g_stationary(K, f, u0, Phi, omega, tol, maxit, r1=1, r2=1, groups=None) -> PCGResult:
     """POD-2G used directly as the iterative solver (Algorithm 2, Section 3.3): repeat
     the two-grid cycle on the current approximation while ||f - K u|| > tol ||f||
     (the guard of Algorithm 2 read as ">"), at most maxit cycles. iters = cycles applied."""
@@ -290,7 +350,7 @@ def pod2g_stationary(K, f, u0, Phi, omega, tol, maxit, r1=1, r2=1) -> PCGResult:
     if fnorm == 0.0:
         return PCGResult(np.zeros(n), 0, OK, 0.0, [0.0])
     try:
-        st = pod2g_setup(K, Phi, omega, r1, r2)
+        st = pod2g_setup(K, Phi, omega, r1, r2, groups)
     except np.linalg.LinAlgError:
         return PCGResult(np.zeros(n) if u0 is None else np.array(u0, float), 0, NOT_SPD, np.nan)
     u = np.zeros(n) if u0 is None else np.array(u0, dtype=np.float64)
@@ -304,7 +364,7 @@ def pod2g_stationary(K, f, u0, Phi, omega, tol, maxit, r1=1, r2=1) -> PCGResult:
             break
         if k >= maxit:
             break
-        u = two_grid_cycle(K, f, u, st.Phi, st.L_c, st.Dinv, omega, r1, r2)
+        u = two_grid_cycle(K, f, u, st.Phi, st.L_c, st.Dinv, omega, r1, r2, groups=groups)
         r = f - K @ u
         k += 1
         hist.append(float(np.linalg.norm(r)) / fnorm)

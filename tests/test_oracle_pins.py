@@ -357,3 +357,82 @@ def test_stationary_special_inputs():
     assert r.iters == 0 and np.all(r.x == 0)
     r = O.pod2g_stationary(K, P.f0, None, Phi, 2 / 3, 1e-14, 3)
     assert r.iters == 3 and r.status == O.NOT_CONVERGED
+
+
+# ----------------------------------------------------------------------------- Gauss-Seidel relaxation
+def _gs_system(kind="q4", ne=4, seed=20):
+    P, K = _small_system(seed, ne=ne, kind=kind)
+    groups = O.multicolour_groups(P.row_ptr, P.col_idx, P.bs)
+    return P, K, groups
+
+
+@pytest.mark.parametrize("kind,ne,colours", [("q1", 6, 4), ("q4", 5, 4), ("hex8", 3, 8)])
+def test_multicolour_groups_are_independent_and_partition(kind, ne, colours):
+    P, K, groups = _gs_system(kind, ne)
+    assert len(groups) == colours * P.bs
+    allg = np.sort(np.concatenate(groups))
+    assert np.array_equal(allg, np.arange(P.n))
+    Kd = K.toarray()
+    for g in groups:
+        sub = Kd[np.ix_(g, g)]
+        assert np.count_nonzero(sub - np.diag(np.diag(sub))) == 0    # no coupling inside a group
+    # structural check on the block pattern: neighbours never share a colour
+    nodecol = np.empty(P.n_nodes, dtype=int)
+    for t, g in enumerate(groups):
+        nodecol[g // P.bs] = t // P.bs
+    rows = np.repeat(np.arange(P.n_nodes), np.diff(P.row_ptr))
+    off = rows != P.col_idx
+    assert np.all(nodecol[rows[off]] != nodecol[P.col_idx[off]])
+
+
+def test_gauss_seidel_sweep_equals_triangular_splitting():
+    from scipy.linalg import solve_triangular
+    P, K, groups = _gs_system("q4", 4)
+    order = np.concatenate(groups)
+    Kd = K.toarray()
+    rng = np.random.default_rng(3)
+    f, u = rng.standard_normal(P.n), rng.standard_normal(P.n)
+    Kp = Kd[np.ix_(order, order)]
+    for reverse, lower in ((False, True), (True, False)):
+        tri = np.tril(Kp) if lower else np.triu(Kp)
+        step = solve_triangular(tri, (f - Kd @ u)[order], lower=lower)
+        want = u.copy()
+        want[order] += step
+        got = O.gauss_seidel(K, K.diagonal(), f, u, groups, 1, reverse=reverse)
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+def test_symmetric_gauss_seidel_cycle_and_preconditioner():
+    P, K, groups = _gs_system("q4", 4, 21)
+    Phi = _basis(K, 3)
+    order = np.concatenate(groups)
+    st = O.pod2g_setup(K, Phi, 1.0, 1, 1, groups)
+    E = O.two_grid_error_operator(K, Phi, st.Dinv, 1.0, order=order)
+    Kd = K.toarray()
+    rng = np.random.default_rng(5)
+    f, u0 = rng.standard_normal(P.n), rng.standard_normal(P.n)
+    xs = np.linalg.solve(Kd, f)
+    u1 = O.two_grid_cycle(K, f, u0, Phi, st.L_c, st.Dinv, 1.0, 1, 1, groups=groups)
+    assert np.allclose(xs - u1, E @ (xs - u0), atol=1e-10 * np.abs(xs).max())
+    app = O.pod2g_preconditioner(K, st)
+    B = np.column_stack([app(e) for e in np.eye(P.n)])
+    assert np.abs(B - B.T).max() < 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+    # planted mistake: forward sweeps on both sides give a non-symmetric cycle
+    fwd = O.gauss_seidel
+    bad = lambda r: (lambda y: fwd(K, K.diagonal(), r, y + Phi @ O.cholesky_solve(st.L_c, Phi.T @ (r - K @ y)),
+                                   groups, 1))(fwd(K, K.diagonal(), r, np.zeros_like(r), groups, 1))
+    Bb = np.column_stack([bad(e) for e in np.eye(P.n)])
+    assert np.abs(Bb - Bb.T).max() > 1e-6 * np.abs(Bb).max()
+
+
+def test_gauss_seidel_smoother_needs_fewer_pcg_iterations():
+    P, K, groups = _gs_system("q1", 24, 22)
+    Phi = _basis(K, 6)
+    f = P.f0
+    jac = O.pod2g_pcg(K, f, None, Phi, 2 / 3, 1e-8, 500)
+    sgs = O.pod2g_pcg(K, f, None, Phi, 1.0, 1e-8, 500, groups=groups)
+    assert jac.status == O.OK and sgs.status == O.OK
+    assert sgs.iters < jac.iters
+    xs = np.linalg.solve(K.toarray(), f)
+    assert np.linalg.norm(sgs.x - xs) <= 1e-6 * np.linalg.norm(xs)
