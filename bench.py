@@ -273,10 +273,15 @@ def gb300_arm(args):
     set_batch = s.set_coeffs_batch_dev if elements else s.set_values_batch_dev
     set_one = s.set_coeffs if elements else s.set_values
 
+    x0_dev = torch.empty_like(b_dev) if args.x0 == "rom" else None
+
     def step():
         st, sts = set_batch(slots, vals)
         assert st == pkg.OK, pkg.strerror(st)
-        iters, rel, status, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=tol, maxit=maxit)
+        if x0_dev is not None:   # POD reduced-order solution as the initial guess
+            st = s.rom_solution_dev(slots, b_dev, x0_dev)
+            assert st == pkg.OK, pkg.strerror(st)
+        iters, rel, status, rc = s.solve_batch_dev(slots, b_dev, x_dev, x0_dev=x0_dev, tol=tol, maxit=maxit)
         assert rc == pkg.OK, (pkg.strerror(rc), status)
         return iters, rel
 
@@ -355,7 +360,13 @@ def gb300_arm(args):
         for _ in range(e2e_steps):
             for i in slots:
                 assert set_one(i, vals_h[i]) == pkg.OK
-            X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=tol, maxit=maxit)
+            if x0_dev is None:
+                X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=tol, maxit=maxit)
+            else:   # the reduced-order initial guess lives on the device: copy b in, x out
+                bd = torch.from_numpy(b_h).to(b_dev.device)
+                assert s.rom_solution_dev(slots, bd, x0_dev) == pkg.OK
+                it_h, rel_h, st_h, rc = s.solve_batch_dev(slots, bd, x_dev, x0_dev=x0_dev, tol=tol, maxit=maxit)
+                X = x_dev.cpu().numpy()
             assert rc == pkg.OK
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         extra["e2e"] = {"value": B / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(vals_h.nbytes + b_h.nbytes),
@@ -405,7 +416,7 @@ def gb300_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
             "config": {"workload": workload_desc(wl, B, tol), "method": method_name(args.method),
-                       "operator": args.operator, "tuning": tuning,
+                       "operator": args.operator, "x0": args.x0, "tuning": tuning,
                        "batch": B, "n": P.n, "nnzb": P.nnzb, "k": wl.spec.k, "parallelism": f"replicas{world}",
                        "l2": (f"inputs larger than L2 ({vals.numel() * 8 / 1e9:.2f} GB FP64 "
                               f"{'coefficients' if elements else 'values'} per step; per-iteration working set "
@@ -473,6 +484,8 @@ def main():
     ap.add_argument("--operator", default="assembled", choices=["assembled", "elements"],
                     help="instances as assembled block values, or as element coefficients (element-factored K)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--x0", default="zero", choices=["zero", "rom"],
+                    help="initial guess: zero, or the POD reduced-order solution Phi K_c^-1 Phi^T b")
     ap.add_argument("--tol", type=float, default=TOL)
     ap.add_argument("--maxit", type=int, default=MAXIT)
     args = ap.parse_args()

@@ -74,6 +74,12 @@ extern "C" {
 #define POD2G_MIXED_FP32PHI  1
 #define POD2G_MIXED_BF16PHI  2
 
+/* relaxation schemes of the two-grid cycle */
+#define POD2G_SMOOTHER_JACOBI 0  /* damped Jacobi u <- u + omega D^-1 (f - K u), pre and post */
+#define POD2G_SMOOTHER_SGS    1  /* pointwise Gauss-Seidel (eq. GaussSeidel) in a multicolour order:
+                                    forward sweeps before, backward sweeps after the coarse
+                                    correction (omega is not used) */
+
 /* solution methods */
 #define POD2G_PCG            0  /* PCG preconditioned by one POD-2G cycle from zero (Algorithm 3) */
 #define POD2G_STATIONARY     1  /* the POD-2G two-grid cycle itself as the iteration (Algorithm 2,
@@ -102,6 +108,11 @@ typedef struct {
     int chunk;                /* PCG iterations per CUDA-graph launch in the batched path (even, default 8) */
     void* stream;             /* cudaStream_t to run on; NULL = a stream owned by the context */
     int method;               /* POD2G_PCG (default) or POD2G_STATIONARY; iters then counts cycles */
+    int smoother;             /* POD2G_SMOOTHER_JACOBI (default) or POD2G_SMOOTHER_SGS. Nodes are
+                                 coloured greedily in index order (smallest colour no lower-index
+                                 neighbour holds); a sweep visits colour 0, 1, .. and within a node
+                                 its components in order (backward: all reversed). Mixed precision
+                                 with SGS: beta_pr must be 0. */
 } pod2g_opts;
 
 /* Fill *opts with defaults. Never fails. */
@@ -183,6 +194,14 @@ int pod2g_solve_batch(pod2g_t ctx, int nslots, const int* slots, const double* c
 int pod2g_solve_batch_dev(pod2g_t ctx, int nslots, const int* slots, const double* b_dev,
                           const double* x0_dev, double tol, int maxit, double* x_dev,
                           int* iters, double* relres, int* status);
+
+/* POD reduced-order solution (Section 3.3, steps 3-4): x_i = Phi K_c^{-1} Phi^T b_i
+ * for set-up slots, with the coarse matrix of each slot's set-up; the
+ * reduced-order approximation that the paper's surrogate stands in for, to be
+ * passed as x0. b_dev, x_dev: nslots consecutive vectors of n doubles (device).
+ * k = 0 gives x = 0. Blocks until done. */
+int pod2g_rom_solution_dev(pod2g_t ctx, int nslots, const int* slots, const double* b_dev,
+                           double* x_dev);
 
 /* Serving. A request carries one instance's values (host, nnzb*bs*bs doubles),
  * its right-hand side and an optional x0 (host, n doubles each); the library

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libpod2g.so")
 OK, NOT_CONVERGED, BREAKDOWN, NOT_SPD, INVALID_ARG, ADMISSION, OOM, CUDA_ERROR, TIMEOUT, NONFINITE, PENDING = range(11)
 FP64, MIXED_FP32PHI, MIXED_BF16PHI = 0, 1, 2
 PCG, STATIONARY = 0, 1  # solution methods: Algorithm 3, or the two-grid cycle of Algorithm 2 iterated
+SMOOTHER_JACOBI, SMOOTHER_SGS = 0, 1  # relaxation: damped Jacobi, or multicolour symmetric Gauss-Seidel
 
 EXPORTS = [
     "pod2g_default_opts", "pod2g_create", "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
@@ -25,6 +26,7 @@ EXPORTS = [
     "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_kernel_timing", "pod2g_kernel_times",
     "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc", "pod2g_device_bytes", "pod2g_create_elements",
     "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev", "pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune",
+    "pod2g_rom_solution_dev",
 ]
 NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
 TOO_LARGE = 11
@@ -49,7 +51,8 @@ class Tuning(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("omega", C.c_double), ("pre", C.c_int), ("post", C.c_int), ("precision", C.c_int),
                 ("beta_pr", C.c_int), ("max_batch", C.c_int), ("hbm_budget", C.c_size_t),
-                ("spin_limit", C.c_int64), ("chunk", C.c_int), ("stream", C.c_void_p), ("method", C.c_int)]
+                ("spin_limit", C.c_int64), ("chunk", C.c_int), ("stream", C.c_void_p), ("method", C.c_int),
+                ("smoother", C.c_int)]
 
 
 _lib = None
@@ -73,6 +76,7 @@ def load_library(path: str = LIB_PATH):
                                           C.POINTER(P)]
     lib.pod2g_set_coeffs.argtypes = [P, I, P, I]
     lib.pod2g_get_tuning.argtypes = [P, C.POINTER(Tuning)]
+    lib.pod2g_rom_solution_dev.argtypes = [P, I, IP, P, P]
     lib.pod2g_set_tuning.argtypes = [P, C.POINTER(Tuning)]
     lib.pod2g_autotune.argtypes = [P, I, IP, P, I, C.POINTER(Tuning)]
     lib.pod2g_set_coeffs_batch_dev.argtypes = [P, I, IP, P, IP]
@@ -101,7 +105,7 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_destroy.restype = None
     lib.pod2g_strerror.argtypes = [I]
     lib.pod2g_strerror.restype = C.c_char_p
-    for name in ("pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune", "pod2g_create", "pod2g_create_elements", "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
+    for name in ("pod2g_rom_solution_dev", "pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune", "pod2g_create", "pod2g_create_elements", "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
                  "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
                  "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
                  "pod2g_serve_stop", "pod2g_info"):
@@ -137,7 +141,7 @@ class Solver:
 
     def __init__(self, row_ptr, col_idx, bs, phi, *, precision=MIXED_FP32PHI, omega=2.0 / 3.0, pre=1, post=1,
                  beta_pr=False, max_batch=1, hbm_budget=0, chunk=8, spin_limit=0, stream=None, method=0,
-                 elements=None):
+                 elements=None, smoother=0):
         """elements: None (instances are given as assembled block values), or a dict with
         conn [n_el, npe] int, k_ref [(npe*bs)^2] float64 and optional fixed [n_brows] bool:
         the element-factored operator, instances given as element coefficients."""
@@ -160,6 +164,7 @@ class Solver:
         o.spin_limit = spin_limit
         o.stream = C.c_void_p(stream) if stream else None
         o.method = method
+        o.smoother = smoother
         h = C.c_void_p()
         if elements is None:
             st = lib.pod2g_create(C.byref(pat), phi_cm.ctypes.data_as(C.POINTER(C.c_double)), k, C.byref(o),
@@ -223,6 +228,15 @@ class Solver:
                 return INVALID_ARG
             st = self._lib.pod2g_set_values(self.h, slot, v.ctypes.data_as(C.c_void_p), 0)
         return st
+
+    def rom_solution_dev(self, slots, b_dev, x_dev) -> int:
+        """POD reduced-order solution Phi K_c^-1 Phi^T b for set-up slots (CUDA float64
+        tensors [len(slots), n]); use it as x0."""
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        if b_dev.numel() != len(slots) * self.n or x_dev.numel() != len(slots) * self.n:
+            return INVALID_ARG
+        return self._lib.pod2g_rom_solution_dev(self.h, len(slots), slots.ctypes.data_as(C.POINTER(C.c_int)),
+                                                C.c_void_p(b_dev.data_ptr()), C.c_void_p(x_dev.data_ptr()))
 
     # -------------------------------------------------------------- launch shapes
     def get_tuning(self):
@@ -318,6 +332,9 @@ class Solver:
         iters = np.zeros(m, dtype=np.int32)
         rel = np.zeros(m)
         status = np.zeros(m, dtype=np.int32)
+        if b_dev.numel() != m * self.n or x_dev.numel() != m * self.n or \
+                (x0_dev is not None and x0_dev.numel() != m * self.n):
+            return iters, rel, status, INVALID_ARG
         rc = self._lib.pod2g_solve_batch_dev(self.h, m, slots.ctypes.data_as(C.POINTER(C.c_int)),
                                              C.c_void_p(b_dev.data_ptr()),
                                              C.c_void_p(x0_dev.data_ptr()) if x0_dev is not None else None, tol, maxit,

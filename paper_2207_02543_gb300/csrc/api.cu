@@ -109,7 +109,7 @@ static void free_all(pod2g_ctx* c) {
                     c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
                     c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
                     c->d_pdf, c->d_qdf, c->d_bdf, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
-                    c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32};
+                    c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32, c->d_cnodes, c->d_colour};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_scal64) cudaFreeHost(c->h_scal64);
@@ -216,6 +216,8 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     if (!(o.omega > 0.0) || o.pre < 0 || o.post < 0 || o.pre > 8 || o.post > 8) return POD2G_INVALID_ARG;
     if (o.precision != POD2G_FP64 && (o.pre > 1 || o.post > 1)) return POD2G_INVALID_ARG;
     if (o.method != POD2G_PCG && o.method != POD2G_STATIONARY) return POD2G_INVALID_ARG;
+    if (o.smoother != POD2G_SMOOTHER_JACOBI && o.smoother != POD2G_SMOOTHER_SGS) return POD2G_INVALID_ARG;
+    if (o.smoother == POD2G_SMOOTHER_SGS && o.precision != POD2G_FP64 && o.beta_pr) return POD2G_INVALID_ARG;
     if (o.chunk <= 0) o.chunk = 8;
     // pattern checks: monotone row_ptr, columns in range and sorted, diagonal present
     const int nb = pat->n_brows;
@@ -255,6 +257,34 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     c->B = o.max_batch; c->omega = o.omega; c->hbm_budget = o.hbm_budget; c->spin_limit = o.spin_limit;
     c->chunk = o.chunk;
     c->method = o.method;
+    c->smoother = o.smoother;
+    std::vector<int32_t> h_cnodes;
+    std::vector<uint8_t> h_colour;
+    if (c->smoother == POD2G_SMOOTHER_SGS) {
+        // greedy colouring in node order: smallest colour held by no lower-index neighbour
+        std::vector<int> col(nb, -1);
+        int ncol = 0;
+        for (int i = 0; i < nb; ++i) {
+            std::vector<char> taken(ncol + 1, 0);
+            for (int t = pat->row_ptr[i]; t < pat->row_ptr[i + 1]; ++t) {
+                const int j = pat->col_idx[t];
+                if (j < i) taken[col[j]] = 1;
+            }
+            int cc = 0;
+            while (taken[cc]) ++cc;
+            col[i] = cc;
+            ncol = std::max(ncol, cc + 1);
+        }
+        if (ncol > 255) { delete c; return POD2G_INVALID_ARG; }
+        c->ncolours = ncol;
+        c->coff.assign(ncol + 1, 0);
+        for (int i = 0; i < nb; ++i) c->coff[col[i] + 1]++;
+        for (int q = 0; q < ncol; ++q) c->coff[q + 1] += c->coff[q];
+        h_cnodes.resize(nb);
+        std::vector<int> fill(c->coff.begin(), c->coff.end() - 1);
+        for (int i = 0; i < nb; ++i) h_cnodes[fill[col[i]]++] = i;
+        h_colour.assign(col.begin(), col.end());
+    }
     if (el) {
         c->elem = 1;
         c->n_el = el->n_elems;
@@ -282,10 +312,14 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     ALLOC(c->d_Lc, sizeof(double) * std::max(1, c->B * k * k));
     ALLOC(c->d_setup_status, sizeof(int) * c->B);
     ALLOC(c->d_stage, sizeof(double) * std::max(tot, (long long)c->n_el));
-    ALLOC(c->d_W, sizeof(double) * std::max(1LL, n * kp));
+    ALLOC(c->d_W, sizeof(double) * (std::max(3LL, n) * std::max(kp, 1) + 64));
     ALLOC(c->d_ac_part, sizeof(double) * std::max(1, 2 * c->num_sms * k * k));
     ALLOC(c->d_Ac, sizeof(double) * std::max(1, k * k));
     ALLOC(c->d_counters, sizeof(unsigned) * CNT_N);
+    if (c->smoother == POD2G_SMOOTHER_SGS) {
+        ALLOC(c->d_cnodes, sizeof(int32_t) * nb);
+        ALLOC(c->d_colour, sizeof(uint8_t) * nb);
+    }
     ALLOC(c->d_iob, sizeof(double) * n * c->B);
     ALLOC(c->d_iox, sizeof(double) * n * c->B);
     if (c->precision == POD2G_FP64) {
@@ -353,6 +387,10 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
                 }
             ok = up(c->d_phi32, h.data(), sizeof(float) * n * kp);
         }
+    }
+    if (ok && c->smoother == POD2G_SMOOTHER_SGS) {
+        ok = up(c->d_cnodes, h_cnodes.data(), sizeof(int32_t) * nb) &&
+             up(c->d_colour, h_colour.data(), sizeof(uint8_t) * nb);
     }
     if (ok && c->elem) {
         ok = up(c->d_desc, h_desc.data(), sizeof(uint64_t) * nnzb) &&
@@ -557,6 +595,12 @@ int pod2g_solve_batch_dev(pod2g_t c, int nslots, const int* slots, const double*
         if (st[i] != POD2G_OK && first == POD2G_OK) first = st[i];
     }
     return first;
+}
+
+int pod2g_rom_solution_dev(pod2g_t c, int nslots, const int* slots, const double* b_dev, double* x_dev) {
+    if (!c || !b_dev || !x_dev || c->serving) return POD2G_INVALID_ARG;
+    P2G_TRY(check_slots(c, nslots, slots));
+    return rom_solution(c, nslots, slots, b_dev, x_dev);
 }
 
 int pod2g_solve_batch(pod2g_t c, int nslots, const int* slots, const double* const* b, const double* const* x0,

@@ -388,14 +388,14 @@ __global__ void k_upd(Dims D, int want, float2* __restrict__ x, float2* __restri
     }
 }
 
-// Pre-relaxation from zero and the residual it leaves: y1 = omega D^-1 r (r1 = 1)
-// or 0 (r1 = 0), r1 = r - K y1, written to out (FP32); cluster partial sums of
-// ||r||^2 go to part[cluster][slot].
+// Pre-relaxation from zero and the residual it leaves: y1 = omega D^-1 r (PRE = 1),
+// 0 (PRE = 0) or a stored y1 (PRE = 2, Gauss-Seidel), r1 = r - K y1, written to
+// out (FP32); cluster partial sums of ||r||^2 go to part[cluster][slot].
 template <int BS, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
           const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
-          float* __restrict__ out, double* part, const SlotScalars* __restrict__ sc) {
+          const float* __restrict__ y1, float* __restrict__ out, double* part, const SlotScalars* __restrict__ sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[POD2G_MAX_BP];
     ELEM_SMEM_KREF(MF, E);
@@ -421,7 +421,7 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
 #pragma unroll
                         for (int cc = 0; cc < BS; ++cc) {
                             const long long o = ((long long)j * BS + cc) * D.Bp + lane;
-                            yj[u][cc] = w * dinv[o] * r[o].x;
+                            yj[u][cc] = PRE == 2 ? y1[o] : w * dinv[o] * r[o].x;
                         }
                         if constexpr (MF) {
                             dsc[u] = __ldg(E.desc + blk);
@@ -611,12 +611,14 @@ __global__ void k_coarse(Dims D, int want, const double* __restrict__ part, cons
     }
 }
 
-// y2 = y1 + Phi e_c with y1 = omega D^-1 r (r1 = 1) or 0; KP a compile-time
-// width so that a row's Phi loads are all issued before they are used.
+// y2 = y1 + Phi e_c with y1 = omega D^-1 r (PRE = 1), 0 (PRE = 0) or stored
+// (PRE = 2; y may alias y1, each element is read before it is written); KP a
+// compile-time width so that a row's Phi loads are all issued before they are used.
 template <int PRE, int KP>
 __global__ void __launch_bounds__(POD2G_THREADS)
-k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restrict__ r, const float* __restrict__ phi,
-       const float* __restrict__ ec, float* __restrict__ y, const SlotScalars* __restrict__ sc, long long n) {
+k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restrict__ r, const float* y1,
+       const float* __restrict__ phi, const float* __restrict__ ec, float* y, const SlotScalars* __restrict__ sc,
+       long long n) {
     extern __shared__ float s_ec[];  // [Bp][KP + 1] (odd row stride: no bank conflicts across slots)
     for (int e = threadIdx.x; e < D.Bp * KP; e += blockDim.x) s_ec[(e / KP) * (KP + 1) + e % KP] = ec[e];
     __syncthreads();
@@ -635,7 +637,7 @@ k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restric
         float4 f[KA / 4];
 #pragma unroll
         for (int m4 = 0; m4 < KP / 4; ++m4) f[m4] = __ldg(ph + m4);
-        float v = PRE ? w * dinv[it] * r[it].x : 0.f;
+        float v = PRE == 2 ? y1[it] : (PRE ? w * dinv[it] * r[it].x : 0.f);
         float v2 = 0.f;
 #pragma unroll
         for (int m4 = 0; m4 < KP / 4; ++m4) {
@@ -645,6 +647,75 @@ k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restric
             v2 = __fmaf_rn(f[m4].w, e_l[4 * m4 + 3], v2);
         }
         y[it] = v + v2;
+    }
+}
+
+// One Gauss-Seidel step over the nodes of one colour (eq. GaussSeidel, pointwise):
+// for each node i of the colour and each component a in order (reverse order if
+// BWD), y_ia += D_ia^-1 (r - K y)_ia, in place. Nodes of one colour share no
+// stored block, so their threads are independent; inside a node the components
+// are updated in sequence, the later rows corrected through the diagonal block.
+// FROM0: the forward sweep from y = 0, where nodes of this and later colours
+// still read as 0 (their memory is not read).
+template <int BS, int MF, int BWD>
+__global__ void __launch_bounds__(POD2G_THREADS, ROW_MINB)
+k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes, int cnt,
+     const uint8_t* __restrict__ col_of, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+     const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
+     float* y, const SlotScalars* __restrict__ sc) {
+    ELEM_SMEM_KREF(MF, E);
+    const int lane = threadIdx.x & (D.Bp - 1);
+    if (sc[lane].state != want) return;
+    const long long items = (long long)cnt << D.lgBp;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int i = cnodes[it >> D.lgBp];
+        float acc[BS], vd[BS * BS];
+#pragma unroll
+        for (int a = 0; a < BS; ++a) acc[a] = 0.f;
+#pragma unroll
+        for (int e = 0; e < BS * BS; ++e) vd[e] = 0.f;
+        float yj[UNROLL][BS], v[UNROLL][BS * BS];
+        int jj[UNROLL];
+        uint64_t dsc[UNROLL];
+        float ce[MF ? POD2G_ELEM_RE : 1];
+        if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
+        row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+            [&](int u, int blk, int j) {
+                jj[u] = j;
+                const bool zero = from0 && (j == i || (int)col_of[j] >= colour);
+#pragma unroll
+                for (int cc = 0; cc < BS; ++cc) yj[u][cc] = zero ? 0.f : y[((long long)j * BS + cc) * D.Bp + lane];
+                if constexpr (MF) {
+                    dsc[u] = __ldg(E.desc + blk);
+                } else {
+                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+#pragma unroll
+                    for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                }
+            },
+            [&](int u) {
+                if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
+#pragma unroll
+                for (int a = 0; a < BS; ++a)
+#pragma unroll
+                    for (int cc = 0; cc < BS; ++cc) acc[a] = __fmaf_rn(v[u][a * BS + cc], yj[u][cc], acc[a]);
+                if (jj[u] == i) {
+#pragma unroll
+                    for (int e = 0; e < BS * BS; ++e) vd[e] = v[u][e];
+                }
+            });
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+            const int a = BWD ? BS - 1 - t : t;
+            const long long o = ((long long)i * BS + a) * D.Bp + lane;
+            const float yo = from0 ? 0.f : y[o];
+            const float dy = dinv[o] * (r[o].x - acc[a]);
+            y[o] = yo + dy;
+#pragma unroll
+            for (int b = 0; b < BS; ++b)
+                if (BWD ? b < a : b > a) acc[b] = __fmaf_rn(vd[b * BS + a], dy, acc[b]);
+        }
     }
 }
 
@@ -777,11 +848,37 @@ int batched_grid(int num_sms, long long items) {
 
 #define KP_LIST(X) X(8) X(16) X(24) X(32) X(40) X(48) X(64)
 
+// Jacobi: y1 = omega D^-1 r on the fly (PRE = r1). Gauss-Seidel: y1 stored in s (PRE = 2) or 0.
 template <int BS, int MF>
 static void launch_smooth1(pod2g_ctx* c, Dims D, int want) {
-    k_smooth1<BS, MF><<<D.G, POD2G_THREADS, 0, c->stream>>>(D, want, c->pre, c->d_row_ptr, c->d_col_idx,
+    const int pre = c->smoother == POD2G_SMOOTHER_SGS ? (c->pre ? 2 : 0) : c->pre;
+    k_smooth1<BS, MF><<<D.G, POD2G_THREADS, 0, c->stream>>>(D, want, pre, c->d_row_ptr, c->d_col_idx,
                                                              c->d_vals32, elem_op(c), c->d_dinv32, c->d_rdf,
-                                                             c->d_y32, c->d_part, c->d_sc);
+                                                             c->d_s32, c->d_y32, c->d_part, c->d_sc);
+}
+
+// Gauss-Seidel sweep over all colours (forward from zero, or backward in place) on s.
+template <int BS, int MF>
+static int launch_gs(pod2g_ctx* c, Dims D, int want, int backward) {
+    const ElemOp E = elem_op(c);
+    for (int t = 0; t < c->ncolours; ++t) {
+        const int col = backward ? c->ncolours - 1 - t : t;
+        const int cnt = c->coff[col + 1] - c->coff[col];
+        if (cnt == 0) continue;
+        const int g = std::max(1, std::min(ceil_div((long long)cnt << D.lgBp, POD2G_THREADS), 8 * c->num_sms));
+        if (backward)
+            k_gs<BS, MF, 1><<<g, POD2G_THREADS, 0, c->stream>>>(D, want, 0, col, c->d_cnodes + c->coff[col], cnt,
+                                                                 c->d_colour, c->d_row_ptr, c->d_col_idx,
+                                                                 c->d_vals32, E, c->d_dinv32, c->d_rdf, c->d_s32,
+                                                                 c->d_sc);
+        else
+            k_gs<BS, MF, 0><<<g, POD2G_THREADS, 0, c->stream>>>(D, want, 1, col, c->d_cnodes + c->coff[col], cnt,
+                                                                 c->d_colour, c->d_row_ptr, c->d_col_idx,
+                                                                 c->d_vals32, E, c->d_dinv32, c->d_rdf, c->d_s32,
+                                                                 c->d_sc);
+        P2G_TRY(pod2g_check_launch(c));
+    }
+    return POD2G_OK;
 }
 
 // slots per thread of the restriction: 4 (vector loads), more when Bp x kp needs it
@@ -813,37 +910,40 @@ static void launch_restrict(pod2g_ctx* c, Dims D, int want) {
 #undef CASE_LB
 }
 
+// y2 = y1 + Phi e_c. Jacobi: y1 recomputed from r (or 0), y2 -> y. Gauss-Seidel: y1
+// stored in s (or 0), y2 -> s in place.
 static void launch_prol(pod2g_ctx* c, Dims D, int want) {
     const size_t sm = sizeof(float) * c->Bp * (c->kp + 1);
     const long long n = c->n;
     const int gp = std::max(1, std::min(ceil_div(n * c->Bp, POD2G_THREADS), c->grid_prol));
-#define CASE_KP(KP_)                                                                                              \
-    case KP_:                                                                                                     \
-        if (c->pre)                                                                                               \
-            k_prol<1, KP_><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,    \
-                                                                 c->d_ec, c->d_y32, c->d_sc, n);                  \
-        else                                                                                                      \
-            k_prol<0, KP_><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,    \
-                                                                 c->d_ec, c->d_y32, c->d_sc, n);                  \
+    const bool gs = c->smoother == POD2G_SMOOTHER_SGS;
+    const int pre = gs ? (c->pre ? 2 : 0) : (c->pre ? 1 : 0);
+    float* out = gs ? c->d_s32 : c->d_y32;
+#define PROL(PRE_, KP_)                                                                                     \
+    k_prol<PRE_, KP_><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_s32,      \
+                                                            c->d_phi32, c->d_ec, out, c->d_sc, n)
+#define CASE_KP(KP_)                                     \
+    case KP_:                                            \
+        if (pre == 2) PROL(2, KP_);                      \
+        else if (pre == 1) PROL(1, KP_);                 \
+        else PROL(0, KP_);                               \
         break;
     switch (c->kp) {
         KP_LIST(CASE_KP)
-        case 0:
-            if (c->pre)
-                k_prol<1, 0><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,
-                                                                   c->d_ec, c->d_y32, c->d_sc, n);
-            else
-                k_prol<0, 0><<<gp, POD2G_THREADS, sm, c->stream>>>(D, want, c->d_dinv32, c->d_rdf, c->d_phi32,
-                                                                   c->d_ec, c->d_y32, c->d_sc, n);
-            break;
+        CASE_KP(0)
     }
 #undef CASE_KP
+#undef PROL
 }
 
 template <int BS, int MF>
 static void launch_post(pod2g_ctx* c, Dims D, int want) {
     dim3 g(D.G), t(POD2G_THREADS);
-    if (c->post)
+    if (c->smoother == POD2G_SMOOTHER_SGS)  // s is final: only r^T s and beta
+        k_post<BS, 0, MF><<<g, t, 0, c->stream>>>(D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, elem_op(c),
+                                                  c->d_dinv32, c->d_rdf, c->d_s32, c->d_s32, c->d_part,
+                                                  c->d_counters + CNT_POST, c->d_sc);
+    else if (c->post)
         k_post<BS, 1, MF><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
                                                   elem_op(c), c->d_dinv32, c->d_rdf, c->d_y32, c->d_s32, c->d_part,
                                                   c->d_counters + CNT_POST, c->d_sc);
@@ -866,6 +966,10 @@ static int elementwise_grid(pod2g_ctx* c, long long total) {
 
 // the preconditioner s = AMG(0; K, r, r1, r2) for lanes in state `want`
 static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
+    const bool gs = c->smoother == POD2G_SMOOTHER_SGS;
+    int st = POD2G_OK;
+    if (gs && c->pre) LAUNCH_BS(st = launch_gs, (c, D, want, 0));   // y1: forward sweep from zero, into s
+    P2G_TRY(st);
     LAUNCH_BS(launch_smooth1, (c, D, want));
     P2G_TRY(mark(c));
     if (c->kp > 0) launch_restrict(c, D, want);
@@ -874,6 +978,8 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
     P2G_TRY(mark(c));
     launch_prol(c, D, want);
     P2G_TRY(mark(c));
+    if (gs && c->post) LAUNCH_BS(st = launch_gs, (c, D, want, 1));  // backward sweep on s in place
+    P2G_TRY(st);
     LAUNCH_BS(launch_post, (c, D, want));
     P2G_TRY(mark(c));
     return POD2G_OK;
@@ -910,6 +1016,7 @@ int batched_alloc(pod2g_ctx* c) {
         const int lb = restrict_lb(c->Bp, c->kp);
         const int sm_p = c->Bp * (c->kp + 1) * (int)sizeof(float);
         const void* fr = nullptr;
+        const void* fp2 = nullptr;
         const void* fp1 = nullptr;
         const void* fp0 = nullptr;
 #define FN_LB(KP_, LB_) \
@@ -917,6 +1024,7 @@ int batched_alloc(pod2g_ctx* c) {
 #define FN_KP(KP_)                                                      \
         LB_LIST(FN_LB, KP_)                                              \
         if (c->kp == KP_) {                                              \
+            fp2 = (const void*)k_prol<2, KP_>;                           \
             fp1 = (const void*)k_prol<1, KP_>;                           \
             fp0 = (const void*)k_prol<0, KP_>;                           \
         }
@@ -925,6 +1033,7 @@ int batched_alloc(pod2g_ctx* c) {
 #undef FN_LB
         if (!fr) return POD2G_INVALID_ARG;
         P2G_CUDA(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_r));
+        P2G_CUDA(cudaFuncSetAttribute(fp2, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
         P2G_CUDA(cudaFuncSetAttribute(fp1, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
         P2G_CUDA(cudaFuncSetAttribute(fp0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
     }
@@ -975,6 +1084,7 @@ static int build_graph(pod2g_ctx* c) {
         c->tev.resize((size_t)c->chunk * 9);
         for (auto& ev : c->tev) P2G_CUDA(cudaEventCreate(&ev));
     }
+    const int64_t l0 = c->launches;
     P2G_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int st = POD2G_OK;
     for (int it = 0; it < c->chunk && st == POD2G_OK; ++it) {
@@ -983,13 +1093,14 @@ static int build_graph(pod2g_ctx* c) {
         st = enqueue_iteration(c, D);
     }
     c->cap_ev = nullptr;
+    c->iter_launches = (c->launches - l0) / c->chunk;
+    c->launches = l0;  // captured, not launched; counted at each replay
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != POD2G_OK) return st;
     P2G_CUDA(e);
     e = cudaGraphInstantiate(&c->graph_exec, g, 0);
     cudaGraphDestroy(g);
     P2G_CUDA(e);
-    c->launches -= (int64_t)8 * c->chunk;  // captured, not launched; counted at each replay
     return POD2G_OK;
 }
 
@@ -998,7 +1109,7 @@ static int build_graph(pod2g_ctx* c) {
 int batched_chunk(pod2g_ctx* c) {
     P2G_TRY(build_graph(c));
     P2G_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
-    c->launches += (int64_t)8 * c->chunk;
+    c->launches += c->iter_launches * c->chunk;
     P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));

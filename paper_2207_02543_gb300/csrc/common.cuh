@@ -51,6 +51,13 @@ struct pod2g_ctx {
     int nb = 0, bs = 0, n = 0, nnzb = 0, k = 0, kp = 0;   // kp: k padded to a multiple of 4
     int precision = 0, pre = 1, post = 1, beta_pr = 0, B = 1, Bp = 1, chunk = 8;
     int method = 0;                     // POD2G_PCG or POD2G_STATIONARY
+    int smoother = 0;                   // POD2G_SMOOTHER_JACOBI or POD2G_SMOOTHER_SGS
+    // multicolour order of the Gauss-Seidel smoother
+    int ncolours = 0;
+    std::vector<int> coff;              // [ncolours + 1] offsets into d_cnodes
+    int32_t* d_cnodes = nullptr;        // [nb] nodes sorted by colour
+    uint8_t* d_colour = nullptr;        // [nb] colour of each node
+    int64_t iter_launches = 8;          // kernels per captured iteration
     double omega = 2.0 / 3.0;
     size_t hbm_budget = 0, allocated = 0;
     int64_t spin_limit = 0;
@@ -340,6 +347,7 @@ int batched_grid(int num_sms, long long items);
 int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, int* iters, double* relres,
                      int* status);
 int batched_alloc(pod2g_ctx* c);
+int rom_solution(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, double* x_dev);
 int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t);
 int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, int iters);
 void batched_free(pod2g_ctx* c);

@@ -122,6 +122,23 @@ __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ s,
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_BETA] = beta;
 }
 
+// One Gauss-Seidel step over the nodes of one colour (FP64, pointwise, eq.
+// GaussSeidel): for each node and each component in order (reverse if bwd),
+// y_d += (f - K y)_d / K_dd with the current y. Nodes of one colour do not couple.
+__global__ void k_gs64(const int32_t* __restrict__ cnodes, int cnt, const int32_t* __restrict__ row_ptr,
+                       const int32_t* __restrict__ col_idx, const double* __restrict__ vals,
+                       const double* __restrict__ dinv, const double* __restrict__ f, double* y, int bs, int bwd) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const int i = cnodes[t];
+        for (int q = 0; q < bs; ++q) {
+            const int a = bwd ? bs - 1 - q : q;
+            const int d = i * bs + a;
+            const double kx = row_dot(row_ptr, col_idx, vals, y, bs, i, a);
+            y[d] += dinv[d] * (f[d] - kx);
+        }
+    }
+}
+
 // x += s (the correction of one stationary two-grid cycle)
 __global__ void k_add(double* __restrict__ x, const double* __restrict__ s, int n) {
     for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) x[d] += s[d];
@@ -207,8 +224,23 @@ static int plain_precond(pod2g_ctx* c, int slot, const double* r, double* s) {
     const double* dinv = c->d_dinv64 + (size_t)slot * n;
     double* y = c->d_y64;
     double* t = c->d_t64;
+    const bool gs = c->smoother == POD2G_SMOOTHER_SGS;
+    auto sweep = [&](int bwd) -> int {
+        for (int q = 0; q < c->ncolours; ++q) {
+            const int col = bwd ? c->ncolours - 1 - q : q;
+            const int cnt = c->coff[col + 1] - c->coff[col];
+            if (cnt == 0) continue;
+            k_gs64<<<std::max(1, std::min(ceil_div(cnt, T), 4 * c->num_sms)), T, 0, c->stream>>>(
+                c->d_cnodes + c->coff[col], cnt, c->d_row_ptr, c->d_col_idx, vals, dinv, r, y, c->bs, bwd);
+            P2G_TRY(pod2g_check_launch(c));
+        }
+        return POD2G_OK;
+    };
     // pre-relaxation from y = 0
-    if (c->pre == 0) {
+    if (gs) {
+        P2G_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, c->stream));
+        for (int it = 0; it < c->pre; ++it) P2G_TRY(sweep(0));
+    } else if (c->pre == 0) {
         P2G_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, c->stream));
     } else {
         k_row<<<G, T, 0, c->stream>>>(ROW_SMOOTH, c->d_row_ptr, c->d_col_idx, vals, dinv, c->omega, nullptr, r, y,
@@ -235,7 +267,10 @@ static int plain_precond(pod2g_ctx* c, int slot, const double* r, double* s) {
         P2G_TRY(pod2g_check_launch(c));
     }
     // post-relaxation; the last sweep writes s
-    if (c->post == 0) {
+    if (gs) {
+        for (int it = 0; it < c->post; ++it) P2G_TRY(sweep(1));
+        P2G_CUDA(cudaMemcpyAsync(s, y, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    } else if (c->post == 0) {
         P2G_CUDA(cudaMemcpyAsync(s, y, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
     } else {
         for (int it = 0; it < c->post; ++it) {

@@ -1,0 +1,86 @@
+"""GPU parity of the POD reduced-order solution x = Phi K_c^-1 Phi^T b (Section 3.3,
+steps 3-4) and of PCG started from it, through the C ABI, against the oracle's
+`rom_solution` / `pod2g_pcg` on the same (rounded) inputs.
+
+The reduced-order solution is a direct projection: relative error <= 1e-9 against
+the oracle (FP64 coarse factor on both sides). PCG from it: the usual parity bar
+(x <= 1e-6 mixed / 1e-7 FP64 at tol 1e-8, iterations +-2), and no more iterations
+than from x0 = 0 (the point of a good initial guess, Section 4.1).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import pod2g_oracle as O  # noqa: E402
+from synth.problems import Workload  # noqa: E402
+from synth.rounding import round_f32, round_phi  # noqa: E402
+from synth.snapshots import pod_basis  # noqa: E402
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2207_02543_gb300 as p
+    return p
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name,precision", [("q4_64", 1), ("hex8_16", 2), ("q1_64", 0)])
+def test_rom_solution_and_pcg_from_it(pkg, name, precision):
+    wl = Workload(name)
+    P, Phi = wl.problem, pod_basis(wl)
+    m = 1 if precision == pkg.FP64 else min(wl.spec.batch, 5)
+    xis = wl.query_thetas(m)
+    Bm = wl.rhs(m)
+    if precision == pkg.FP64:
+        vals, phi_used, xtol = [wl.values(xi) for xi in xis], Phi, 1e-7
+    else:
+        vals = [round_f32(wl.values(xi)) for xi in xis]
+        phi_used, xtol = round_phi(Phi, "bf16" if precision == pkg.MIXED_BF16PHI else "f32"), 1e-6
+    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=precision, omega=wl.spec.omega, max_batch=m)
+    for i in range(m):
+        assert s.set_values(i, vals[i]) == pkg.OK
+    slots = list(range(m))
+    b_dev = torch.from_numpy(Bm).cuda()
+    x0 = torch.empty_like(b_dev)
+    assert s.rom_solution_dev(slots, b_dev, x0) == pkg.OK
+    x0h = x0.cpu().numpy()
+    x = torch.empty_like(b_dev)
+    it, rel, st, rc = s.solve_batch_dev(slots, b_dev, x, x0_dev=x0, tol=TOL, maxit=5000)
+    assert rc == pkg.OK
+    it0, _, _, rc0 = s.solve_batch_dev(slots, b_dev, torch.empty_like(b_dev), tol=TOL, maxit=5000)
+    assert rc0 == pkg.OK
+    xh = x.cpu().numpy()
+    for i in range(m):
+        K = P.csr(vals[i])
+        rom = O.rom_solution(K, phi_used, Bm[i])
+        assert _relerr(x0h[i], rom) <= 1e-9
+        ref = O.pod2g_pcg(K, Bm[i], rom, phi_used, wl.spec.omega, TOL, 5000)
+        assert ref.status == O.OK and st[i] == pkg.OK
+        assert abs(it[i] - ref.iters) <= 2
+        assert _relerr(xh[i], ref.x) <= xtol
+        assert it[i] <= it0[i]
+    s.close()
+
+
+def test_rom_solution_without_coarse_space_is_zero(pkg):
+    wl = Workload("q4_16")
+    P = wl.problem
+    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, np.zeros((P.n, 0)), omega=wl.spec.omega, max_batch=2)
+    for i in range(2):
+        assert s.set_values(i, round_f32(wl.values(wl.query_thetas(2)[i]))) == pkg.OK
+    b = torch.from_numpy(wl.rhs(2)).cuda()
+    x = torch.full_like(b, 7.0)
+    assert s.rom_solution_dev([0, 1], b, x) == pkg.OK
+    assert torch.count_nonzero(x).item() == 0
+    s.close()
