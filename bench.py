@@ -93,7 +93,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False):
+def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False, sgs=False):
     """Algorithmic HBM bytes per kernel of the batched iteration (values FP32, vectors
     double-float 8 B, s/y/D^-1 FP32 4 B, Phi FP32 read once per launch, col_idx
     once per launch, per-slot scalars and partials negligible). Element operator:
@@ -116,6 +116,12 @@ def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False):
     }
     shared = {"k_p": 0, "k_spmv": pat, "k_upd": 0, "k_smooth1": pat, "k_restrict": phi,
               "k_coarse": G // 8 * Bp * (k_pad + 2) * 8, "k_prol": phi, "k_post": pat}
+    if sgs:   # timing groups: forward sweeps + residual; stored y1; backward sweeps + r^T s
+        per_lane["k_smooth1"] = 2 * vals + n * (20 + 16)
+        per_lane["k_prol"] = n * (4 + 4)
+        per_lane["k_post"] = vals + n * (20 + 16)
+        shared["k_smooth1"] = 2 * pat
+        shared["k_post"] = pat
     return {name: per_lane[name] * lane_iters + shared[name] * launches for name in per_lane}
 
 
@@ -131,11 +137,11 @@ NCU_TRAFFIC = {
 NCU_SOURCE = {("q4_512", 64, "assembled"): "profiles/launches_q4_512_b64.md"}
 
 
-def run_oracle(mode, inst, timeout=900, workload=WORKLOAD, tol=TOL, method="pcg"):
+def run_oracle(mode, inst, timeout=900, workload=WORKLOAD, tol=TOL, method="pcg", smoother="jacobi"):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    r = subprocess.run([sys.executable, "-m", "oracle.timing", workload, str(inst), str(mode), str(tol), method],
+    r = subprocess.run([sys.executable, "-m", "oracle.timing", workload, str(inst), str(mode), str(tol), method, smoother],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -267,8 +273,9 @@ def gb300_arm(args):
     method = pkg.STATIONARY if args.method == "stationary" else pkg.PCG
     tol, maxit = args.tol, args.maxit
     el = dict(conn=P.conn, k_ref=P.Kref, fixed=P.clamped if P.dirichlet == "identity" else None) if elements else None
+    smoother = pkg.SMOOTHER_SGS if args.smoother == "sgs" else pkg.SMOOTHER_JACOBI
     s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=precision, omega=wl.spec.omega,
-                   max_batch=B, stream=stream.cuda_stream, method=method, elements=el)
+                   max_batch=B, stream=stream.cuda_stream, method=method, elements=el, smoother=smoother)
     slots = list(range(B))
     set_batch = s.set_coeffs_batch_dev if elements else s.set_values_batch_dev
     set_one = s.set_coeffs if elements else s.set_values
@@ -333,7 +340,7 @@ def gb300_arm(args):
     G = max(1, min((P.n_nodes * Bp + 255) // 256, 4 * torch.cuda.get_device_properties(local).multi_processor_count))
     kp = {0: 0}.get(wl.spec.k, [v for v in (0, 8, 16, 24, 32, 40, 48, 64) if v >= wl.spec.k][0])
     nl = {k: v[1] for k, v in ktimes.items()}
-    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp, elements)
+    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp, elements, args.smoother == "sgs")
     rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     tot_k = sum(v[0] for v in ktimes.values())
@@ -374,7 +381,7 @@ def gb300_arm(args):
         # plain FP64 one-at-a-time baseline on the same GPU
         if not args.no_plain:
             sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1,
-                            method=method)
+                            method=method, smoother=smoother)
             vals_plain = vals if not elements else wl.values_torch(xis[:2], device="cuda").reshape(2, -1)
             nplain = 2
             times, its = [], []
@@ -397,7 +404,7 @@ def gb300_arm(args):
         # CPU baseline: the oracle on a bounded sample (single thread)
         if not args.no_cpu:
             try:
-                o = run_oracle(100, 0, workload=args.workload, tol=tol, method=args.method)
+                o = run_oracle(100, 0, workload=args.workload, tol=tol, method=args.method, smoother=args.smoother)
                 it_full = int(iters[0])
                 cpu_val = 1.0 / (o["seconds_per_iteration"] * it_full)
                 extra["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -416,7 +423,7 @@ def gb300_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
             "config": {"workload": workload_desc(wl, B, tol), "method": method_name(args.method),
-                       "operator": args.operator, "x0": args.x0, "tuning": tuning,
+                       "operator": args.operator, "smoother": args.smoother, "x0": args.x0, "tuning": tuning,
                        "batch": B, "n": P.n, "nnzb": P.nnzb, "k": wl.spec.k, "parallelism": f"replicas{world}",
                        "l2": (f"inputs larger than L2 ({vals.numel() * 8 / 1e9:.2f} GB FP64 "
                               f"{'coefficients' if elements else 'values'} per step; per-iteration working set "
@@ -484,6 +491,8 @@ def main():
     ap.add_argument("--operator", default="assembled", choices=["assembled", "elements"],
                     help="instances as assembled block values, or as element coefficients (element-factored K)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "sgs"],
+                    help="relaxation of the two-grid cycle: damped Jacobi or multicolour symmetric Gauss-Seidel")
     ap.add_argument("--x0", default="zero", choices=["zero", "rom"],
                     help="initial guess: zero, or the POD reduced-order solution Phi K_c^-1 Phi^T b")
     ap.add_argument("--tol", type=float, default=TOL)

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE: started by bench.py in fresh single-threaded processes
 (BLAS threads pinned to 1), never by the solver library.
 
-    python -m oracle.timing <workload> <instance> <iterations|full> <tol> [pcg|stationary]
+    python -m oracle.timing <workload> <instance> <iterations|full> <tol> [pcg|stationary] [jacobi|sgs]
 
 prints one JSON object: seconds, iterations run, seconds per iteration, and for
 a full solve the iteration count and the true relative residual.
@@ -19,6 +19,7 @@ import time
 def main(argv):
     name, inst, mode, tol = argv[0], int(argv[1]), argv[2], float(argv[3])
     method = argv[4] if len(argv) > 4 else "pcg"
+    smoother = argv[5] if len(argv) > 5 else "jacobi"
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)
@@ -39,7 +40,9 @@ def main(argv):
     maxit = 100000 if mode == "full" else int(mode)
     t0 = time.perf_counter()
     solve = O.pod2g_pcg if method == "pcg" else O.pod2g_stationary
-    res = solve(K, b, None, phi, wl.spec.omega, tol if mode == "full" else 0.0, maxit)
+    P = wl.problem
+    groups = O.multicolour_groups(P.row_ptr, P.col_idx, P.bs) if smoother == "sgs" else None
+    res = solve(K, b, None, phi, wl.spec.omega, tol if mode == "full" else 0.0, maxit, groups=groups)
     dt = time.perf_counter() - t0
     out = dict(workload=name, instance=inst, seconds=dt, iterations=res.iters,
                seconds_per_iteration=dt / max(res.iters, 1), status=res.status, relres=res.relres,

@@ -171,6 +171,40 @@ __device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, 
         __syncthreads();                                                         \
     }
 
+// ---------------------------------------------------------------------------- bulk copies (cp.async.bulk + mbarrier)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> own shared memory, completion counted in bytes on `bar`; 16-byte
+// aligned addresses and a size that is a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// Wait for the phase with the given parity to complete, at most `limit` polls;
+// false if it did not.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit) {
+    const uint32_t a = smem_addr(bar);
+    for (unsigned t = 0; t < limit; ++t) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+#define MBAR_POLLS (1u << 22)  // bound on the polls of one wait (each poll may suspend briefly)
+
 // ---------------------------------------------------------------------------- load / store / residual
 // Joining lanes: b -> bdf, x0 -> xdf (zero if absent), p = q = 0.
 __global__ void k_load(const double* __restrict__ b, const double* __restrict__ x0, const int* __restrict__ slots,
@@ -537,6 +571,122 @@ k_restrict(Dims D, int want, long long n, const float* __restrict__ phi, const f
     cluster_store(s_c, NOUT, cpart + (long long)(blockIdx.x / CLUSTER) * NOUT);
 }
 
+// The same restriction with the CTA's contiguous rows of r1 ([n][Bp]) and Phi
+// ([n][KP]) staged through shared memory: chunks of R rows are copied with
+// cp.async.bulk into a ring of RS_STAGES buffers (one mbarrier each) while the
+// teams consume earlier chunks, so the loads of a thread no longer wait on HBM
+// latency. A wait that exceeds its poll bound sets *err, waits (bounded) for the
+// copies still in flight and skips the rest of the work; every CTA still takes
+// part in the cluster reduction, so nothing waits forever.
+#define RS_STAGES 3
+template <int KP, int LB>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_restrict_bulk(Dims D, long long n, int R, const float* __restrict__ phi, const float* __restrict__ r1,
+                double* cpart, int* err) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    __shared__ int s_bad;
+    const int Bp = D.Bp;
+    const int NOUT = Bp * KP;
+    const int quads = Bp / LB, groups = KP / 8;
+    const int team_size = quads * groups;
+    const int teams = POD2G_THREADS / team_size;
+    const int team = threadIdx.x / team_size, w = threadIdx.x - team * team_size;
+    const int q = w % quads, g = w / quads;
+    const int b0 = q * LB, m0 = g * 8;
+    double* s_c = reinterpret_cast<double*>(s_raw);
+    float* s_team = reinterpret_cast<float*>(s_c + NOUT);
+    float* s_r = s_team + teams * NOUT;
+    float* s_p = s_r + RS_STAGES * R * Bp;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_p + RS_STAGES * R * KP);
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long d_begin = blockIdx.x * per, d_end = min(n, d_begin + per);
+    const int nchunks = d_end > d_begin ? (int)((d_end - d_begin + R - 1) / R) : 0;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        for (int st = 0; st < RS_STAGES; ++st) mbar_init(bars + st, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int issued = 0;  // meaningful in thread 0
+    auto issue = [&](int ch) {
+        const int st = ch % RS_STAGES;
+        const long long d0 = d_begin + (long long)ch * R;
+        const int rows = (int)min((long long)R, d_end - d0);
+        const unsigned br = (unsigned)rows * Bp * 4u, bq = (unsigned)rows * KP * 4u;
+        mbar_expect_tx(bars + st, br + bq);
+        bulk_load(s_r + (size_t)st * R * Bp, r1 + d0 * Bp, br, bars + st);
+        bulk_load(s_p + (size_t)st * R * KP, phi + d0 * KP, bq, bars + st);
+    };
+    if (threadIdx.x == 0)
+        for (; issued < min(nchunks, RS_STAGES); ++issued) issue(issued);
+    float acc[LB][8];
+#pragma unroll
+    for (int l = 0; l < LB; ++l)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[l][m] = 0.f;
+    int bad_chunk = -1;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int st = ch % RS_STAGES;
+        if (!mbar_wait(bars + st, (unsigned)(ch / RS_STAGES) & 1u, MBAR_POLLS)) s_bad = 1;
+        const int rows = (int)min((long long)R, d_end - (d_begin + (long long)ch * R));
+        if (team < teams) {
+            const float* rb = s_r + (size_t)st * R * Bp + b0;
+            const float* pb = s_p + (size_t)st * R * KP + m0;
+            for (int t = team; t < rows; t += teams) {
+                float x[LB];
+                if (LB == 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp);
+                    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+                } else if (LB == 8) {
+                    const float4 v0 = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp);
+                    const float4 v1 = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp + 4);
+                    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+                    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+                } else {
+#pragma unroll
+                    for (int l = 0; l < LB; ++l) x[l] = rb[(size_t)t * Bp + l];
+                }
+                const float4 f0 = *reinterpret_cast<const float4*>(pb + (size_t)t * KP);
+                const float4 f1 = *reinterpret_cast<const float4*>(pb + (size_t)t * KP + 4);
+                const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+                for (int l = 0; l < LB; ++l)
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) acc[l][m] = __fmaf_rn(f[m], x[l], acc[l][m]);
+            }
+        }
+        __syncthreads();  // buffer st is free again
+        if (s_bad) {
+            bad_chunk = ch;
+            break;
+        }
+        if (threadIdx.x == 0 && issued < nchunks) issue(issued++);
+    }
+    if (bad_chunk >= 0) {
+        // a copy did not complete in time: report, let the copies in flight land, skip the rest
+        if (threadIdx.x == 0) {
+            atomicExch(err, 2);
+            for (int ch = bad_chunk; ch < issued; ++ch)
+                mbar_wait(bars + ch % RS_STAGES, (unsigned)(ch / RS_STAGES) & 1u, MBAR_POLLS);
+        }
+        __syncthreads();
+    }
+    if (team < teams) {
+#pragma unroll
+        for (int l = 0; l < LB; ++l)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) s_team[team * NOUT + (b0 + l) * KP + m0 + m] = acc[l][m];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
+        double sum = 0.0;
+        for (int t = 0; t < teams; ++t) sum += (double)s_team[t * NOUT + o];
+        s_c[o] = sum;
+    }
+    __syncthreads();
+    cluster_store(s_c, NOUT, cpart + (long long)(blockIdx.x / CLUSTER) * NOUT);
+}
+
 // One CTA per slot: convergence test on ||r||^2, coarse right-hand side
 // c = Phi^T r1 (sum over partial rows in order), e_c = L^-T L^-1 c in FP64.
 __global__ void k_coarse(Dims D, int want, const double* __restrict__ part, const double* __restrict__ cpart,
@@ -895,15 +1045,39 @@ static size_t restrict_smem(int Bp, int kp) {
 }
 static int restrict_grid(pod2g_ctx* c) { return c->grid_restrict; }
 
+// Bulk-staged restriction: rows per chunk (~24 KB of r1 and Phi per stage, a
+// multiple of 4) and its shared memory; 0 when it does not apply (Bp < 4: rows
+// of r1 are not 16-byte multiples) or does not fit.
+static int restrict_bulk_rows(int Bp, int kp) {
+    if (kp == 0 || Bp < 4) return 0;
+    int R = 24576 / ((Bp + kp) * 4);
+    R = std::max(8, std::min(128, R)) / 4 * 4;
+    return R;
+}
+static size_t restrict_bulk_smem(int Bp, int kp) {
+    const int R = restrict_bulk_rows(Bp, kp);
+    if (R == 0) return 0;
+    const size_t sz = restrict_smem(Bp, kp) + (size_t)RS_STAGES * R * (Bp + kp) * sizeof(float) +
+                      RS_STAGES * sizeof(uint64_t);
+    return sz <= 200 * 1024 ? sz : 0;
+}
+
 #define LB_LIST(X, KP) X(KP, 1) X(KP, 2) X(KP, 4) X(KP, 8)
 static void launch_restrict(pod2g_ctx* c, Dims D, int want) {
-    const size_t sm = restrict_smem(c->Bp, c->kp);
+    const size_t smb = restrict_bulk_smem(c->Bp, c->kp);
+    const size_t sm = smb ? smb : restrict_smem(c->Bp, c->kp);
+    const int R = restrict_bulk_rows(c->Bp, c->kp);
     const int g = D.NPc * CLUSTER;
     const int lb = restrict_lb(c->Bp, c->kp);
 #define CASE_LB(KP_, LB_)                                                                                          \
-    if (c->kp == KP_ && lb == LB_)                                                                                 \
-        k_restrict<KP_, LB_><<<g, POD2G_THREADS, sm, c->stream>>>(D, want, c->n, c->d_phi32, c->d_y32, c->d_cpart, \
-                                                                  c->d_sc);
+    if (c->kp == KP_ && lb == LB_) {                                                                               \
+        if (smb)                                                                                                   \
+            k_restrict_bulk<KP_, LB_><<<g, POD2G_THREADS, sm, c->stream>>>(D, c->n, R, c->d_phi32, c->d_y32,       \
+                                                                           c->d_cpart, c->d_err);                  \
+        else                                                                                                       \
+            k_restrict<KP_, LB_><<<g, POD2G_THREADS, sm, c->stream>>>(D, want, c->n, c->d_phi32, c->d_y32,         \
+                                                                      c->d_cpart, c->d_sc);                        \
+    }
 #define CASE_KP(KP_) LB_LIST(CASE_LB, KP_)
     KP_LIST(CASE_KP)
 #undef CASE_KP
@@ -1012,15 +1186,18 @@ int batched_alloc(pod2g_ctx* c) {
     c->grid_prol = 8 * c->num_sms;
     c->grid_vec = 8 * c->num_sms;
     if (c->precision != POD2G_FP64 && c->kp > 0) {
-        const int sm_r = (int)restrict_smem(c->Bp, c->kp);
+        const int sm_r = (int)(restrict_bulk_smem(c->Bp, c->kp) ? restrict_bulk_smem(c->Bp, c->kp)
+                                                                 : restrict_smem(c->Bp, c->kp));
         const int lb = restrict_lb(c->Bp, c->kp);
         const int sm_p = c->Bp * (c->kp + 1) * (int)sizeof(float);
         const void* fr = nullptr;
         const void* fp2 = nullptr;
         const void* fp1 = nullptr;
         const void* fp0 = nullptr;
-#define FN_LB(KP_, LB_) \
-        if (c->kp == KP_ && lb == LB_) fr = (const void*)k_restrict<KP_, LB_>;
+#define FN_LB(KP_, LB_)                                                                    \
+        if (c->kp == KP_ && lb == LB_)                                                     \
+            fr = restrict_bulk_smem(c->Bp, c->kp) ? (const void*)k_restrict_bulk<KP_, LB_> \
+                                                  : (const void*)k_restrict<KP_, LB_>;
 #define FN_KP(KP_)                                                      \
         LB_LIST(FN_LB, KP_)                                              \
         if (c->kp == KP_) {                                              \
