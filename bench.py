@@ -293,11 +293,16 @@ def gb300_arm(args):
         return iters, rel
 
     tuning = None
-    if not args.no_autotune:
+    if args.tuning:
+        # a given launch shape (e.g. the one an earlier autotuned run reported), no autotuning
+        shape = {f"grid_{k}": int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))}
+        assert s.set_tuning(**shape) == pkg.OK, shape
+        tuning = s.get_tuning()
+    elif not args.no_autotune:
         # launch shapes picked by timing candidates on this workload (outside the timed region)
         st, sts = set_batch(slots, vals)
         assert st == pkg.OK, pkg.strerror(st)
-        st, tuning = s.autotune(slots, b_dev, iters=16)
+        st, tuning = s.autotune(slots, b_dev, iters=32)
         assert st == pkg.OK, pkg.strerror(st)
     torch.cuda.synchronize()
     for _ in range(max(args.warmup, 0)):
@@ -491,6 +496,8 @@ def main():
     ap.add_argument("--operator", default="assembled", choices=["assembled", "elements"],
                     help="instances as assembled block values, or as element coefficients (element-factored K)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--tuning", default="", help="launch shape to use instead of autotuning, "
+                    "e.g. rows=1216,spmv=1216,restrict=456,prol=608,vec=1216")
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "sgs"],
                     help="relaxation of the two-grid cycle: damped Jacobi or multicolour symmetric Gauss-Seidel")
     ap.add_argument("--x0", default="zero", choices=["zero", "rom"],

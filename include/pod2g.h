@@ -290,10 +290,11 @@ int pod2g_solve_noalloc(int32_t n_brows, int32_t bs, int32_t nnzb, const int32_t
  * kernel group. A shape changes only the grouping of partial sums, so results are
  * deterministic for a given shape and differ between shapes at rounding level. */
 typedef struct {
-    int32_t grid_rows;      /* sparse row kernels (SpMV, smoothers, residual): multiple of 8, 8..8*SMs */
+    int32_t grid_rows;      /* smoother / residual row kernels: multiple of 8, 8..8*SMs */
     int32_t grid_restrict;  /* restriction Phi^T r: multiple of 8, 8..4*SMs */
     int32_t grid_prol;      /* prolongation: 1..8*SMs */
     int32_t grid_vec;       /* vector updates (p; x and r): 1..8*SMs */
+    int32_t grid_spmv;      /* outer SpMV q = K p: multiple of 8, 8..8*SMs */
 } pod2g_tuning;
 
 /* Current shape (mixed contexts; FP64 contexts return POD2G_INVALID_ARG). */

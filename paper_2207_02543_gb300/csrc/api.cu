@@ -460,6 +460,7 @@ int pod2g_get_tuning(pod2g_t c, pod2g_tuning* out) {
     out->grid_restrict = c->grid_restrict;
     out->grid_prol = c->grid_prol;
     out->grid_vec = c->grid_vec;
+    out->grid_spmv = c->grid_spmv;
     return POD2G_OK;
 }
 

@@ -58,6 +58,7 @@ namespace {
 struct Dims {
     int nb, Bp, lgBp, k, kp, G, NP;  // NP = G / CLUSTER partial-sum rows of the row kernels
     int NPc;                         // partial-sum rows of the restriction
+    int NPs;                         // partial-sum rows of the outer SpMV (its own grid)
     int stat;                        // 1: stationary two-grid iteration (alpha = 1, beta = 0)
     double omega;
 };
@@ -389,8 +390,8 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
     }
     cta_lane_sum((double)dh + (double)dl, D.Bp, s_tmp, s_out);
     cluster_store(s_out, D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
-    if (!last_cluster_arrive(counter, D.NP)) return;
-    double pq = grid_lane_total(part, D.NP, 2 * D.Bp, D.Bp, s_tmp);
+    if (!last_cluster_arrive(counter, D.NPs)) return;
+    double pq = grid_lane_total(part, D.NPs, 2 * D.Bp, D.Bp, s_tmp);
     if ((int)threadIdx.x < D.Bp) {
         SlotScalars& s = sc[threadIdx.x];
         if (s.state == want) {
@@ -969,6 +970,7 @@ static Dims dims_of(pod2g_ctx* c) {
     D.kp = c->kp;
     D.G = c->grid_rows;
     D.NP = c->grid_rows / CLUSTER;
+    D.NPs = c->grid_spmv / CLUSTER;
     D.NPc = restrict_grid(c) / CLUSTER;
     D.stat = c->method == POD2G_STATIONARY;
     D.omega = c->omega;
@@ -1167,7 +1169,7 @@ static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     k_p<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_s32, c->d_pdf, c->d_sc, total);
     P2G_TRY(mark(c));
     const ElemOp E = elem_op(c);
-    LAUNCH_BS(k_spmv, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx, c->d_vals32,
+    LAUNCH_BS(k_spmv, <<<c->grid_spmv, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx, c->d_vals32,
                                                              E, c->d_pdf, c->d_qdf, c->d_part,
                                                              c->d_counters + CNT_SPMV, c->d_sc));
     P2G_TRY(mark(c));
@@ -1182,6 +1184,7 @@ int batched_alloc(pod2g_ctx* c) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c->num_sms = sms > 0 ? sms : 152;
     c->grid_rows = batched_grid(c->num_sms, (long long)c->nb * c->Bp);
+    c->grid_spmv = c->grid_rows;
     c->grid_restrict = batched_grid(c->num_sms, (long long)2 * c->num_sms * POD2G_THREADS);
     c->grid_prol = 8 * c->num_sms;
     c->grid_vec = 8 * c->num_sms;
@@ -1365,9 +1368,11 @@ int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, 
 int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
     const int sms = c->num_sms;
     if (t->grid_rows < CLUSTER || t->grid_rows % CLUSTER || t->grid_rows > 8 * sms) return POD2G_INVALID_ARG;
+    if (t->grid_spmv < CLUSTER || t->grid_spmv % CLUSTER || t->grid_spmv > 8 * sms) return POD2G_INVALID_ARG;
     if (t->grid_restrict < CLUSTER || t->grid_restrict % CLUSTER || t->grid_restrict > 4 * sms) return POD2G_INVALID_ARG;
     if (t->grid_prol < 1 || t->grid_prol > 8 * sms || t->grid_vec < 1 || t->grid_vec > 8 * sms) return POD2G_INVALID_ARG;
     c->grid_rows = t->grid_rows;
+    c->grid_spmv = t->grid_spmv;
     c->grid_restrict = t->grid_restrict;
     c->grid_prol = t->grid_prol;
     c->grid_vec = t->grid_vec;
@@ -1380,8 +1385,8 @@ int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
 
 // Autotuner: run `iters` iterations of the given (set-up) slots for each of a few
 // candidate launch shapes, timing every kernel with CUDA events inside the graph,
-// and keep per kernel group the fastest shape: row kernels (k_spmv + k_smooth1 +
-// k_post), restriction, prolongation, vector updates (k_p + k_upd). The slots are
+// and keep per kernel group the fastest shape: outer SpMV, smoother row kernels
+// (k_smooth1 + k_post), restriction, prolongation, vector updates (k_p + k_upd). The slots are
 // left idle. The result depends on measured times; a given shape gives
 // deterministic results, and shapes differ only in the summation order of partials.
 int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, int iters) {
@@ -1394,6 +1399,7 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
     pod2g_tuning cand[NC];
     for (int j = 0; j < NC; ++j) {
         cand[j].grid_rows = r8(row_f[j] * sms, need_rows);
+        cand[j].grid_spmv = cand[j].grid_rows;
         cand[j].grid_restrict = r8(res_f[j] * sms, 4 * sms);
         cand[j].grid_prol = std::min(vec_f[j] * sms, need_vec);
         cand[j].grid_vec = std::min(vec_f[j] * sms, need_vec);
@@ -1402,7 +1408,7 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
     std::vector<double> tol(nslots, 0.0);
     std::vector<int> maxit(nslots, iters + 16 * c->chunk);
     std::vector<int> lanes(slots, slots + nslots);
-    double t_rows[NC], t_res[NC], t_prol[NC], t_vec[NC];
+    double t_rows[NC], t_spmv[NC], t_res[NC], t_prol[NC], t_vec[NC];
     for (int j = 0; j < NC; ++j) {
         P2G_TRY(batched_set_tuning(c, &cand[j]));
         P2G_TRY(batched_set_timing(c, 1));
@@ -1410,7 +1416,8 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
         for (int it = 0; it < iters; it += c->chunk) P2G_TRY(batched_chunk(c));
         auto per = [&](int k) { return c->kt_n[k] ? c->kt_ms[k] / (double)c->kt_n[k] : 0.0; };
         t_vec[j] = per(0) + per(2);               // k_p, k_upd
-        t_rows[j] = per(1) + per(3) + per(7);     // k_spmv, k_smooth1, k_post
+        t_spmv[j] = per(1);                       // k_spmv
+        t_rows[j] = per(3) + per(7);              // k_smooth1, k_post
         t_res[j] = per(4);                        // k_restrict
         t_prol[j] = per(6);                       // k_prol
     }
@@ -1422,6 +1429,7 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
     };
     pod2g_tuning pick;
     pick.grid_rows = cand[best(t_rows)].grid_rows;
+    pick.grid_spmv = cand[best(t_spmv)].grid_spmv;
     pick.grid_restrict = cand[best(t_res)].grid_restrict;
     pick.grid_prol = cand[best(t_prol)].grid_prol;
     pick.grid_vec = cand[best(t_vec)].grid_vec;

@@ -127,6 +127,7 @@ struct pod2g_ctx {
     double* d_iob = nullptr;            // [B][n] staging of right-hand sides (host-buffer entry points)
     double* d_iox = nullptr;            // [B][n] staging of x0 / x
     int grid_rows = 0;                  // CTAs of the row kernels (multiple of the cluster size 8)
+    int grid_spmv = 0;                  // CTAs of the outer SpMV (multiple of 8)
     int grid_restrict = 0;              // CTAs of the restriction (multiple of 8)
     int grid_prol = 0;                  // CTAs of the prolongation
     int grid_vec = 0;                   // CTAs of the vector updates (p, x/r)

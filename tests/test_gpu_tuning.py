@@ -51,6 +51,7 @@ def test_autotune_then_solve_matches_oracle(pkg):
     assert st == pkg.OK
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert shape["grid_rows"] % 8 == 0 and 8 <= shape["grid_rows"] <= 8 * sms
+    assert shape["grid_spmv"] % 8 == 0 and 8 <= shape["grid_spmv"] <= 8 * sms
     assert shape["grid_restrict"] % 8 == 0 and 8 <= shape["grid_restrict"] <= 4 * sms
     assert 1 <= shape["grid_prol"] <= 8 * sms and 1 <= shape["grid_vec"] <= 8 * sms
     assert s.get_tuning() == shape
@@ -68,7 +69,7 @@ def test_shapes_deterministic_and_within_tolerance(pkg):
     P, Phi = wl.problem, pod_basis(wl)
     m = wl.spec.batch
     Bm = wl.rhs(m)
-    small = dict(grid_rows=8, grid_restrict=8, grid_prol=1, grid_vec=1)
+    small = dict(grid_rows=8, grid_restrict=8, grid_prol=1, grid_vec=1, grid_spmv=16)
     res = []
     for shape in (small, small, None):
         s, vals = _solver(pkg, wl, Phi, m)
@@ -88,6 +89,7 @@ def test_invalid_shapes_rejected(pkg):
     P, Phi = wl.problem, pod_basis(wl)
     s, _ = _solver(pkg, wl, Phi, 2)
     assert s.set_tuning(grid_rows=12) == pkg.INVALID_ARG          # not a multiple of 8
+    assert s.set_tuning(grid_spmv=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_restrict=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_vec=10 ** 6) == pkg.INVALID_ARG
     s.close()
