@@ -2,8 +2,8 @@
 
 2D plane-stress Q4 on a 512 x 512 grid (526,338 unknowns, 2,362,369 blocks), POD basis
 k = 20 from 200 snapshots, 64 instances solved together exactly as bench.py does
-(device-resident FP64 values through pod2g_set_values_batch_dev, pod2g_solve_batch_dev,
-tol 1e-8). Checks:
+(device-resident FP64 values through pod2g_set_values_batch_dev, launch shapes from
+pod2g_autotune, pod2g_solve_batch_dev, tol 1e-8). Checks:
   * every instance: status OK, the library's final residual equals an independent
     FP64 CPU residual ||b - K x|| / ||b|| of the returned x (K from the FP32-rounded
     values the mixed path solves), and it is <= 1.05e-8;
@@ -47,6 +47,9 @@ def _run_batch(pkg, name, sample):
     s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=prec, omega=wl.spec.omega, max_batch=B)
     slots = list(range(B))
     st, sts = s.set_values_batch_dev(slots, vals)
+    assert st == pkg.OK
+    # the launch shapes bench.py times: picked by the autotuner on this workload
+    st, shape = s.autotune(slots, b, iters=32)
     assert st == pkg.OK
     iters, rel, status, rc = s.solve_batch_dev(slots, b, x, tol=TOL, maxit=5000)
     s.close()
