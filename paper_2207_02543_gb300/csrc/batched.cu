@@ -634,7 +634,8 @@ k_restrict_bulk(Dims D, long long n, int R, const float* __restrict__ phi, const
     const int q = w % quads, g = w / quads;
     const int b0 = q * LB, m0 = g * 8;
     double* s_c = reinterpret_cast<double*>(s_raw);
-    float* s_r = reinterpret_cast<float*>(s_c + NOUT);
+    float* s_team = reinterpret_cast<float*>(s_c + NOUT);
+    float* s_r = s_team + teams * NOUT;
     float* s_p = s_r + RS_STAGES * R * Bp;
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_p + RS_STAGES * R * KP);
     const long long per = (n + gridDim.x - 1) / gridDim.x;
@@ -645,7 +646,6 @@ k_restrict_bulk(Dims D, long long n, int R, const float* __restrict__ phi, const
         for (int st = 0; st < RS_STAGES; ++st) mbar_init(bars + st, 1);
         mbar_fence_init();
     }
-    for (int o = threadIdx.x; o < NOUT; o += blockDim.x) s_c[o] = 0.0;
     __syncthreads();
     int issued = 0;  // meaningful in thread 0
     auto issue = [&](int ch) {
@@ -664,29 +664,6 @@ k_restrict_bulk(Dims D, long long n, int R, const float* __restrict__ phi, const
     for (int l = 0; l < LB; ++l)
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[l][m] = 0.f;
-    auto load_row = [&](const float* rb, const float* pb, int t, float* x, float* f) {
-        if (LB == 4) {
-            const float4 v = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp);
-            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-        } else if (LB == 8) {
-            const float4 v0 = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp);
-            const float4 v1 = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp + 4);
-            x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-            x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-        } else {
-#pragma unroll
-            for (int l = 0; l < LB; ++l) x[l] = rb[(size_t)t * Bp + l];
-        }
-        const float4 f0 = *reinterpret_cast<const float4*>(pb + (size_t)t * KP);
-        const float4 f1 = *reinterpret_cast<const float4*>(pb + (size_t)t * KP + 4);
-        f[0] = f0.x; f[1] = f0.y; f[2] = f0.z; f[3] = f0.w; f[4] = f1.x; f[5] = f1.y; f[6] = f1.z; f[7] = f1.w;
-    };
-    auto fma_row = [&](const float* x, const float* f) {
-#pragma unroll
-        for (int l = 0; l < LB; ++l)
-#pragma unroll
-            for (int m = 0; m < 8; ++m) acc[l][m] = __fmaf_rn(f[m], x[l], acc[l][m]);
-    };
     int bad_chunk = -1;
     for (int ch = 0; ch < nchunks; ++ch) {
         const int st = ch % RS_STAGES;
@@ -695,18 +672,27 @@ k_restrict_bulk(Dims D, long long n, int R, const float* __restrict__ phi, const
         if (team < teams) {
             const float* rb = s_r + (size_t)st * R * Bp + b0;
             const float* pb = s_p + (size_t)st * R * KP + m0;
-            int t = team;
-            for (; t + teams < rows; t += 2 * teams) {  // two rows in flight
-                float xa[LB], fa[8], xb[LB], fb[8];
-                load_row(rb, pb, t, xa, fa);
-                load_row(rb, pb, t + teams, xb, fb);
-                fma_row(xa, fa);
-                fma_row(xb, fb);
-            }
-            if (t < rows) {
-                float xa[LB], fa[8];
-                load_row(rb, pb, t, xa, fa);
-                fma_row(xa, fa);
+            for (int t = team; t < rows; t += teams) {
+                float x[LB];
+                if (LB == 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp);
+                    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+                } else if (LB == 8) {
+                    const float4 v0 = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp);
+                    const float4 v1 = *reinterpret_cast<const float4*>(rb + (size_t)t * Bp + 4);
+                    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+                    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+                } else {
+#pragma unroll
+                    for (int l = 0; l < LB; ++l) x[l] = rb[(size_t)t * Bp + l];
+                }
+                const float4 f0 = *reinterpret_cast<const float4*>(pb + (size_t)t * KP);
+                const float4 f1 = *reinterpret_cast<const float4*>(pb + (size_t)t * KP + 4);
+                const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+                for (int l = 0; l < LB; ++l)
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) acc[l][m] = __fmaf_rn(f[m], x[l], acc[l][m]);
             }
         }
         __syncthreads();  // buffer st is free again
@@ -725,16 +711,19 @@ k_restrict_bulk(Dims D, long long n, int R, const float* __restrict__ phi, const
         }
         __syncthreads();
     }
-    // team partials summed in FP64 in team order (no staging buffer)
-    for (int tm = 0; tm < teams; ++tm) {
-        if (team == tm) {
+    if (team < teams) {
 #pragma unroll
-            for (int l = 0; l < LB; ++l)
+        for (int l = 0; l < LB; ++l)
 #pragma unroll
-                for (int m = 0; m < 8; ++m) s_c[(b0 + l) * KP + m0 + m] += (double)acc[l][m];
-        }
-        __syncthreads();
+            for (int m = 0; m < 8; ++m) s_team[team * NOUT + (b0 + l) * KP + m0 + m] = acc[l][m];
     }
+    __syncthreads();
+    for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
+        double sum = 0.0;
+        for (int t = 0; t < teams; ++t) sum += (double)s_team[t * NOUT + o];
+        s_c[o] = sum;
+    }
+    __syncthreads();
     cluster_store(s_c, NOUT, cpart + (long long)(blockIdx.x / CLUSTER) * NOUT);
 }
 
@@ -1102,14 +1091,14 @@ static int restrict_grid(pod2g_ctx* c) { return c->grid_restrict; }
 // of r1 are not 16-byte multiples) or does not fit.
 static int restrict_bulk_rows(int Bp, int kp) {
     if (kp == 0 || Bp < 4) return 0;
-    int R = 12288 / ((Bp + kp) * 4);
+    int R = 24576 / ((Bp + kp) * 4);
     R = std::max(8, std::min(128, R)) / 4 * 4;
     return R;
 }
 static size_t restrict_bulk_smem(int Bp, int kp) {
     const int R = restrict_bulk_rows(Bp, kp);
     if (R == 0) return 0;
-    const size_t sz = (size_t)Bp * kp * sizeof(double) + (size_t)RS_STAGES * R * (Bp + kp) * sizeof(float) +
+    const size_t sz = restrict_smem(Bp, kp) + (size_t)RS_STAGES * R * (Bp + kp) * sizeof(float) +
                       RS_STAGES * sizeof(uint64_t);
     return sz <= 200 * 1024 ? sz : 0;
 }
