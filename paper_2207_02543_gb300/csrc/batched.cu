@@ -162,50 +162,39 @@ __device__ __forceinline__ float2 df_of(float a) { return make_float2(a, 0.f); }
 #endif
 #define RB_SLOTS(U) (ROW_PIPE ? 2 * (U) : (U))
 template <int U = UNROLL, class Fetch, class Use>
-__device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, const int32_t* __restrict__ aux,
-                                           int b0, int b1, Fetch fetch, Use use) {
-    // aux (may be null): a per-block word loaded together with the column index, so that
-    // loads addressed through it are not one more dependent step behind
+__device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, int b0, int b1, Fetch fetch, Use use) {
     if (!ROW_PIPE) {
         for (int blk0 = b0; blk0 < b1; blk0 += U) {
-            int jj[U], aa[U];
+            int jj[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool in = blk0 + u < b1;
-                jj[u] = in ? __ldg(col_idx + blk0 + u) : -1;
-                aa[u] = (in && aux) ? __ldg(aux + blk0 + u) : 0;
-            }
+            for (int u = 0; u < U; ++u) jj[u] = (blk0 + u < b1) ? __ldg(col_idx + blk0 + u) : -1;
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (jj[u] >= 0) fetch(u, blk0 + u, jj[u], aa[u]);
+                if (jj[u] >= 0) fetch(u, blk0 + u, jj[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (jj[u] >= 0) use(u);
         }
         return;
     }
-    int ja[U], jb[U], xa[U], xb[U];
-    auto issue = [&](int blk0, int* jj, int* aa, int base) {
+    int ja[U], jb[U];
+    auto issue = [&](int blk0, int* jj, int base) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool in = blk0 + u < b1;
-            jj[u] = in ? __ldg(col_idx + blk0 + u) : -1;
-            aa[u] = (in && aux) ? __ldg(aux + blk0 + u) : 0;
-        }
+        for (int u = 0; u < U; ++u) jj[u] = (blk0 + u < b1) ? __ldg(col_idx + blk0 + u) : -1;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (jj[u] >= 0) fetch(base + u, blk0 + u, jj[u], aa[u]);
+            if (jj[u] >= 0) fetch(base + u, blk0 + u, jj[u]);
     };
     if (b0 >= b1) return;
-    issue(b0, ja, xa, 0);
+    issue(b0, ja, 0);
     for (int blk0 = b0; blk0 < b1; blk0 += 2 * U) {
         const bool second = blk0 + U < b1;
-        if (second) issue(blk0 + U, jb, xb, U);
+        if (second) issue(blk0 + U, jb, U);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (ja[u] >= 0) use(u);
         if (second) {
-            if (blk0 + 2 * U < b1) issue(blk0 + 2 * U, ja, xa, 0);
+            if (blk0 + 2 * U < b1) issue(blk0 + 2 * U, ja, 0);
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (jb[u] >= 0) use(U + u);
@@ -216,10 +205,10 @@ __device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, 
 // Assembled FP32 values of block blk for one slot lane: full storage, or symmetric
 // storage (the upper-store block, transposed for a block below the diagonal).
 template <int BS, int VS>
-__device__ __forceinline__ void load_block_values(const float* __restrict__ vals, int map_word, int blk, int Bp,
-                                                  int lane, float* v) {
+__device__ __forceinline__ void load_block_values(const float* __restrict__ vals, const int32_t* __restrict__ upidx,
+                                                  int blk, int Bp, int lane, float* v) {
     if constexpr (VS == VS_SYM) {
-        const uint32_t ui = (uint32_t)map_word;
+        const uint32_t ui = (uint32_t)__ldg(upidx + blk);
         const float* vb = vals + (long long)(ui & ~SYM_T) * BS * BS * Bp + lane;
         if (ui & SYM_T) {
 #pragma unroll
@@ -337,14 +326,14 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
             uint64_t dsc[RB_SLOTS(UNROLL_DF)];
             float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
             if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
-            row_blocks<UNROLL_DF>(col_idx, VS == VS_SYM ? E.upidx : nullptr, row_ptr[i], row_ptr[i + 1],
-                [&](int u, int blk, int j, int a_) {
+            row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
+                [&](int u, int blk, int j) {
 #pragma unroll
                     for (int cc = 0; cc < BS; ++cc) xj[u][cc] = x[((long long)j * BS + cc) * D.Bp + lane];
                     if constexpr (VS == VS_ELEM) {
                         dsc[u] = __ldg(E.desc + blk);
                     } else {
-                        load_block_values<BS, VS>(vals, a_, blk, D.Bp, lane, v[u]);
+                        load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
                     }
                 },
                 [&](int u) {
@@ -426,14 +415,14 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
             uint64_t dsc[RB_SLOTS(UNROLL_DF)];
             float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
             if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
-            row_blocks<UNROLL_DF>(col_idx, VS == VS_SYM ? E.upidx : nullptr, row_ptr[i], row_ptr[i + 1],
-                [&](int u, int blk, int j, int a_) {
+            row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
+                [&](int u, int blk, int j) {
 #pragma unroll
                     for (int cc = 0; cc < BS; ++cc) pj[u][cc] = p[((long long)j * BS + cc) * D.Bp + lane];
                     if constexpr (VS == VS_ELEM) {
                         dsc[u] = __ldg(E.desc + blk);
                     } else {
-                        load_block_values<BS, VS>(vals, a_, blk, D.Bp, lane, v[u]);
+                        load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
                     }
                 },
                 [&](int u) {
@@ -519,8 +508,8 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
                 uint64_t dsc[RB_SLOTS(UNROLL)];
                 float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
                 if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
-                row_blocks(col_idx, VS == VS_SYM ? E.upidx : nullptr, row_ptr[i], row_ptr[i + 1],
-                    [&](int u, int blk, int j, int a_) {
+                row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+                    [&](int u, int blk, int j) {
 #pragma unroll
                         for (int cc = 0; cc < BS; ++cc) {
                             const long long o = ((long long)j * BS + cc) * D.Bp + lane;
@@ -529,7 +518,7 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
                         if constexpr (VS == VS_ELEM) {
                             dsc[u] = __ldg(E.desc + blk);
                         } else {
-                            load_block_values<BS, VS>(vals, a_, blk, D.Bp, lane, v[u]);
+                            load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
                         }
                     },
                     [&](int u) {
@@ -897,8 +886,8 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
         uint64_t dsc[RB_SLOTS(UNROLL)];
         float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
         if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
-        row_blocks(col_idx, VS == VS_SYM ? E.upidx : nullptr, row_ptr[i], row_ptr[i + 1],
-            [&](int u, int blk, int j, int a_) {
+        row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+            [&](int u, int blk, int j) {
                 jj[u] = j;
                 const bool zero = from0 && (j == i || (int)col_of[j] >= colour);
 #pragma unroll
@@ -906,7 +895,7 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
                 if constexpr (VS == VS_ELEM) {
                     dsc[u] = __ldg(E.desc + blk);
                 } else {
-                    load_block_values<BS, VS>(vals, a_, blk, D.Bp, lane, v[u]);
+                    load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
                 }
             },
             [&](int u) {
@@ -961,14 +950,14 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
                 uint64_t dsc[RB_SLOTS(UNROLL)];
                 float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
                 if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
-                row_blocks(col_idx, VS == VS_SYM ? E.upidx : nullptr, row_ptr[i], row_ptr[i + 1],
-                    [&](int u, int blk, int j, int a_) {
+                row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
+                    [&](int u, int blk, int j) {
 #pragma unroll
                         for (int cc = 0; cc < BS; ++cc) yj[u][cc] = y[((long long)j * BS + cc) * D.Bp + lane];
                         if constexpr (VS == VS_ELEM) {
                             dsc[u] = __ldg(E.desc + blk);
                         } else {
-                            load_block_values<BS, VS>(vals, a_, blk, D.Bp, lane, v[u]);
+                            load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
                         }
                     },
                     [&](int u) {
