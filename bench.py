@@ -96,18 +96,13 @@ def measured_peaks():
 def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False, sgs=False):
     """Algorithmic HBM bytes per kernel of the batched iteration (values FP32, vectors
     double-float 8 B, s/y/D^-1 FP32 4 B, Phi FP32 read once per launch, col_idx
-    once per launch, per-slot scalars and partials negligible). Assembled values are
-    stored for the blocks on and above the diagonal (plus a 4-byte block map per launch);
-    the blocks below are their transposes, re-read from L2. Element operator:
+    once per launch, per-slot scalars and partials negligible). Element operator:
     per slot 4 B per element coefficient instead of the block values, plus the
     8 B block descriptors and the row element lists once per launch."""
-    import numpy as np
     P = wl.problem
     n, nnzb, bs = P.n, P.nnzb, P.bs
-    rows = np.repeat(np.arange(P.n_nodes), np.diff(P.row_ptr))
-    nnzb_up = int(np.sum(P.col_idx >= rows))     # symmetric storage: blocks on and above the diagonal
-    vals = P.n_el * 4 if elements else nnzb_up * bs * bs * 4
-    pat = nnzb * 4 + (P.n_nodes + 1) * 4 + ((nnzb * 8 + P.n_nodes * 8 * 4) if elements else nnzb * 4)
+    vals = P.n_el * 4 if elements else nnzb * bs * bs * 4
+    pat = nnzb * 4 + (P.n_nodes + 1) * 4 + ((nnzb * 8 + P.n_nodes * 8 * 4) if elements else 0)
     phi = n * k_pad * 4
     per_lane = {  # bytes per active instance-iteration
         "k_p": n * (4 + 8 + 8),
@@ -134,8 +129,8 @@ def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False, sgs=Fal
 # workload named (profiles/launches_q4_512_b64.md); valid only for the kernel
 # versions that capture measured.
 NCU_TRAFFIC = {
-    ("q4_512", 64, "assembled"): {"k_upd": 1569.2e6, "k_restrict": 185.5e6, "k_prol": 568.5e6, "k_p": 615.7e6,
-                                  "k_coarse": 1.0e6},
+    ("q4_512", 64, "assembled"): {"k_spmv": 3156.2e6, "k_smooth1": 2964.0e6, "k_post": 3100.1e6, "k_upd": 1569.2e6,
+                                  "k_restrict": 185.5e6, "k_prol": 568.5e6, "k_p": 615.7e6, "k_coarse": 1.0e6},
 }
 
 

@@ -109,7 +109,7 @@ static void free_all(pod2g_ctx* c) {
                     c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
                     c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
                     c->d_pdf, c->d_qdf, c->d_bdf, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
-                    c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32, c->d_cnodes, c->d_colour, c->d_upidx, c->d_upfull};
+                    c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32, c->d_cnodes, c->d_colour};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_scal64) cudaFreeHost(c->h_scal64);
@@ -258,39 +258,6 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     c->chunk = o.chunk;
     c->method = o.method;
     c->smoother = o.smoother;
-    // symmetric storage of the assembled values when the pattern is structurally symmetric
-    std::vector<int32_t> h_upidx, h_upfull;
-    if (!el && c->precision != POD2G_FP64) {
-        bool symm = true;
-        std::vector<int32_t> upos(nnzb, -1);
-        int32_t nup = 0;
-        for (int i = 0; i < nb; ++i)
-            for (int t = pat->row_ptr[i]; t < pat->row_ptr[i + 1]; ++t)
-                if (pat->col_idx[t] >= i) upos[t] = nup++;
-        h_upidx.assign(nnzb, 0);
-        h_upfull.assign(nup, 0);
-        for (int i = 0; i < nb && symm; ++i)
-            for (int t = pat->row_ptr[i]; t < pat->row_ptr[i + 1]; ++t) {
-                const int j = pat->col_idx[t];
-                if (j >= i) {
-                    h_upidx[t] = upos[t];
-                    h_upfull[upos[t]] = t;
-                    continue;
-                }
-                const int32_t* cj = pat->col_idx + pat->row_ptr[j];
-                const int nj = pat->row_ptr[j + 1] - pat->row_ptr[j];
-                const int32_t* hit = std::lower_bound(cj, cj + nj, i);
-                if (hit == cj + nj || *hit != i) { symm = false; break; }
-                h_upidx[t] = (int32_t)(upos[pat->row_ptr[j] + (hit - cj)] | (int32_t)SYM_T);
-            }
-        if (symm) {
-            c->sym = 1;
-            c->nnzb_up = nup;
-        } else {
-            h_upidx.clear();
-            h_upfull.clear();
-        }
-    }
     std::vector<int32_t> h_cnodes;
     std::vector<uint8_t> h_colour;
     if (c->smoother == POD2G_SMOOTHER_SGS) {
@@ -373,10 +340,6 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
             ALLOC(c->d_rowel, sizeof(int32_t) * nb * POD2G_ELEM_RE);
             ALLOC(c->d_kref32, sizeof(float) * h_kref.size());
             ALLOC(c->d_coef32, sizeof(float) * (size_t)c->n_el * Bp);
-        } else if (c->sym) {
-            ALLOC(c->d_upidx, sizeof(int32_t) * nnzb);
-            ALLOC(c->d_upfull, sizeof(int32_t) * c->nnzb_up);
-            ALLOC(c->d_vals32, sizeof(float) * (size_t)c->nnzb_up * bs * bs * Bp);
         } else {
             ALLOC(c->d_vals32, sizeof(float) * tot * Bp);
         }
@@ -425,10 +388,6 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
             ok = up(c->d_phi32, h.data(), sizeof(float) * n * kp);
         }
     }
-    if (ok && c->sym) {
-        ok = up(c->d_upidx, h_upidx.data(), sizeof(int32_t) * nnzb) &&
-             up(c->d_upfull, h_upfull.data(), sizeof(int32_t) * c->nnzb_up);
-    }
     if (ok && c->smoother == POD2G_SMOOTHER_SGS) {
         ok = up(c->d_cnodes, h_cnodes.data(), sizeof(int32_t) * nb) &&
              up(c->d_colour, h_colour.data(), sizeof(uint8_t) * nb);
@@ -442,9 +401,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     if (ok && c->precision != POD2G_FP64) {
         ok = cudaMemset(c->d_sc, 0, sizeof(SlotScalars) * Bp) == cudaSuccess &&
              cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
-             (c->elem || cudaMemset(c->d_vals32, 0,
-                                    sizeof(float) * (c->sym ? (size_t)c->nnzb_up * bs * bs : (size_t)tot) * Bp) ==
-                             cudaSuccess) &&
+             (c->elem || cudaMemset(c->d_vals32, 0, sizeof(float) * tot * Bp) == cudaSuccess) &&
              cudaMemset(c->d_dinv32, 0, sizeof(float) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_xdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_rdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&

@@ -202,29 +202,7 @@ __device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, 
     }
 }
 
-// Assembled FP32 values of block blk for one slot lane: full storage, or symmetric
-// storage (the upper-store block, transposed for a block below the diagonal).
-template <int BS, int VS>
-__device__ __forceinline__ void load_block_values(const float* __restrict__ vals, const int32_t* __restrict__ upidx,
-                                                  int blk, int Bp, int lane, float* v) {
-    if constexpr (VS == VS_SYM) {
-        const uint32_t ui = (uint32_t)__ldg(upidx + blk);
-        const float* vb = vals + (long long)(ui & ~SYM_T) * BS * BS * Bp + lane;
-        if (ui & SYM_T) {
-#pragma unroll
-            for (int e = 0; e < BS * BS; ++e) v[e] = vb[((e % BS) * BS + e / BS) * Bp];
-        } else {
-#pragma unroll
-            for (int e = 0; e < BS * BS; ++e) v[e] = vb[e * Bp];
-        }
-    } else {
-        const float* vb = vals + (long long)blk * BS * BS * Bp + lane;
-#pragma unroll
-        for (int e = 0; e < BS * BS; ++e) v[e] = vb[e * Bp];
-    }
-}
-
-// Element kernels (VS_ELEM) stage the FP32 reference sub-blocks in shared memory
+// Element kernels (MF = 1) stage the FP32 reference sub-blocks in shared memory
 // (read with warp-uniform addresses); assembled kernels read per-slot values.
 #define ELEM_SMEM_KREF(MF, E)                                                    \
     __shared__ float s_kref[(MF) ? POD2G_KREF_MAX : 1];                          \
@@ -302,14 +280,14 @@ __global__ void k_store(double* __restrict__ x, const int* __restrict__ slots, i
 // r = b - K x in double-float for masked lanes. init: writes r, sums ||b||^2 and
 // sets tol2 = tol^2 ||b||^2 (b = 0 or non-finite -> DONE). final: sums
 // ||b - K x||^2 into relres.
-template <int BS, int VS>
+template <int BS, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB_DF)
 k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __restrict__ row_ptr,
         const int32_t* __restrict__ col_idx, const float* __restrict__ vals, ElemOp E, const float2* __restrict__ x,
         const float2* __restrict__ b, float2* __restrict__ r, double* part, unsigned* counter, SlotScalars* sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[2 * POD2G_MAX_BP];
-    ELEM_SMEM_KREF(VS == VS_ELEM, E);
+    ELEM_SMEM_KREF(MF, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = mask[lane] != 0;
     float bh = 0.f, bl = 0.f, rh = 0.f, rl = 0.f;
@@ -324,20 +302,22 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
             float2 xj[RB_SLOTS(UNROLL_DF)][BS];
             float v[RB_SLOTS(UNROLL_DF)][BS * BS];
             uint64_t dsc[RB_SLOTS(UNROLL_DF)];
-            float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
-            if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
+            float ce[MF ? POD2G_ELEM_RE : 1];
+            if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
                 [&](int u, int blk, int j) {
 #pragma unroll
                     for (int cc = 0; cc < BS; ++cc) xj[u][cc] = x[((long long)j * BS + cc) * D.Bp + lane];
-                    if constexpr (VS == VS_ELEM) {
+                    if constexpr (MF) {
                         dsc[u] = __ldg(E.desc + blk);
                     } else {
-                        load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
+                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+#pragma unroll
+                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                     }
                 },
                 [&](int u) {
-                    if constexpr (VS == VS_ELEM) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
+                    if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                     for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -391,14 +371,14 @@ __global__ void k_p(Dims D, int want, const float* __restrict__ s, float2* __res
 }
 
 // q = K p (double-float), partial p^T q; last cluster: alpha per slot.
-template <int BS, int VS>
+template <int BS, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB_DF)
 k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
        const float* __restrict__ vals, ElemOp E, const float2* __restrict__ p, float2* __restrict__ q, double* part,
        unsigned* counter, SlotScalars* sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[POD2G_MAX_BP];
-    ELEM_SMEM_KREF(VS == VS_ELEM, E);
+    ELEM_SMEM_KREF(MF, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float dh = 0.f, dl = 0.f;
@@ -413,20 +393,22 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
             float2 pj[RB_SLOTS(UNROLL_DF)][BS];
             float v[RB_SLOTS(UNROLL_DF)][BS * BS];
             uint64_t dsc[RB_SLOTS(UNROLL_DF)];
-            float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
-            if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
+            float ce[MF ? POD2G_ELEM_RE : 1];
+            if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
                 [&](int u, int blk, int j) {
 #pragma unroll
                     for (int cc = 0; cc < BS; ++cc) pj[u][cc] = p[((long long)j * BS + cc) * D.Bp + lane];
-                    if constexpr (VS == VS_ELEM) {
+                    if constexpr (MF) {
                         dsc[u] = __ldg(E.desc + blk);
                     } else {
-                        load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
+                        const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+#pragma unroll
+                        for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                     }
                 },
                 [&](int u) {
-                    if constexpr (VS == VS_ELEM) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
+                    if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                     for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -483,14 +465,14 @@ __global__ void k_upd(Dims D, int want, float2* __restrict__ x, float2* __restri
 // Pre-relaxation from zero and the residual it leaves: y1 = omega D^-1 r (PRE = 1),
 // 0 (PRE = 0) or a stored y1 (PRE = 2, Gauss-Seidel), r1 = r - K y1, written to
 // out (FP32); cluster partial sums of ||r||^2 go to part[cluster][slot].
-template <int BS, int VS>
+template <int BS, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
           const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
           const float* __restrict__ y1, float* __restrict__ out, double* part, const SlotScalars* __restrict__ sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[POD2G_MAX_BP];
-    ELEM_SMEM_KREF(VS == VS_ELEM, E);
+    ELEM_SMEM_KREF(MF, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float rr = 0.f;
@@ -506,8 +488,8 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
             if (PRE) {
                 float yj[RB_SLOTS(UNROLL)][BS], v[RB_SLOTS(UNROLL)][BS * BS];
                 uint64_t dsc[RB_SLOTS(UNROLL)];
-                float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
-                if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
+                float ce[MF ? POD2G_ELEM_RE : 1];
+                if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
                     [&](int u, int blk, int j) {
 #pragma unroll
@@ -515,14 +497,16 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
                             const long long o = ((long long)j * BS + cc) * D.Bp + lane;
                             yj[u][cc] = PRE == 2 ? y1[o] : w * dinv[o] * r[o].x;
                         }
-                        if constexpr (VS == VS_ELEM) {
+                        if constexpr (MF) {
                             dsc[u] = __ldg(E.desc + blk);
                         } else {
-                            load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
+                            const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+#pragma unroll
+                            for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                         }
                     },
                     [&](int u) {
-                        if constexpr (VS == VS_ELEM) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
+                        if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                         for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -863,13 +847,13 @@ k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restric
 // are updated in sequence, the later rows corrected through the diagonal block.
 // FROM0: the forward sweep from y = 0, where nodes of this and later colours
 // still read as 0 (their memory is not read).
-template <int BS, int VS, int BWD>
+template <int BS, int MF, int BWD>
 __global__ void __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes, int cnt,
      const uint8_t* __restrict__ col_of, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
      const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
      float* y, const SlotScalars* __restrict__ sc) {
-    ELEM_SMEM_KREF(VS == VS_ELEM, E);
+    ELEM_SMEM_KREF(MF, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     if (sc[lane].state != want) return;
     const long long items = (long long)cnt << D.lgBp;
@@ -884,22 +868,24 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
         float yj[RB_SLOTS(UNROLL)][BS], v[RB_SLOTS(UNROLL)][BS * BS];
         int jj[RB_SLOTS(UNROLL)];
         uint64_t dsc[RB_SLOTS(UNROLL)];
-        float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
-        if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
+        float ce[MF ? POD2G_ELEM_RE : 1];
+        if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
         row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
             [&](int u, int blk, int j) {
                 jj[u] = j;
                 const bool zero = from0 && (j == i || (int)col_of[j] >= colour);
 #pragma unroll
                 for (int cc = 0; cc < BS; ++cc) yj[u][cc] = zero ? 0.f : y[((long long)j * BS + cc) * D.Bp + lane];
-                if constexpr (VS == VS_ELEM) {
+                if constexpr (MF) {
                     dsc[u] = __ldg(E.desc + blk);
                 } else {
-                    load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
+                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+#pragma unroll
+                    for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                 }
             },
             [&](int u) {
-                if constexpr (VS == VS_ELEM) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
+                if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                 for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -925,14 +911,14 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
 
 // s = y2 + omega D^-1 (r - K y2) (r2 = 1) or y2 (r2 = 0); partial r^T s (and
 // r^T s_old for Polak-Ribiere); last cluster: beta, JOINING -> ACTIVE.
-template <int BS, int POST, int VS>
+template <int BS, int POST, int MF>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
 k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
        const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
        const float* __restrict__ y, float* __restrict__ s, double* part, unsigned* counter, SlotScalars* sc) {
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[2 * POD2G_MAX_BP];
-    ELEM_SMEM_KREF(VS == VS_ELEM && POST, E);
+    ELEM_SMEM_KREF(MF && POST, E);
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float h = 0.f, l = 0.f, xh = 0.f, xl = 0.f;
@@ -948,20 +934,22 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
             if (POST) {
                 float yj[RB_SLOTS(UNROLL)][BS], v[RB_SLOTS(UNROLL)][BS * BS];
                 uint64_t dsc[RB_SLOTS(UNROLL)];
-                float ce[VS == VS_ELEM ? POD2G_ELEM_RE : 1];
-                if constexpr (VS == VS_ELEM) elem_row_coefs(E, i, lane, D.Bp, ce);
+                float ce[MF ? POD2G_ELEM_RE : 1];
+                if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
                     [&](int u, int blk, int j) {
 #pragma unroll
                         for (int cc = 0; cc < BS; ++cc) yj[u][cc] = y[((long long)j * BS + cc) * D.Bp + lane];
-                        if constexpr (VS == VS_ELEM) {
+                        if constexpr (MF) {
                             dsc[u] = __ldg(E.desc + blk);
                         } else {
-                            load_block_values<BS, VS>(vals, E.upidx, blk, D.Bp, lane, v[u]);
+                            const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+#pragma unroll
+                            for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                         }
                     },
                     [&](int u) {
-                        if constexpr (VS == VS_ELEM) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
+                        if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
 #pragma unroll
                         for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -1035,33 +1023,33 @@ int batched_grid(int num_sms, long long items) {
     return ceil_div(g, CLUSTER) * CLUSTER;
 }
 
-// KERNEL<BS, VS> for the context's block size and value source (full, element-factored, symmetric)
-#define LAUNCH_VS(KERNEL, VS_, ...)                                                    \
-    do {                                                                               \
-        if (c->bs == 1) KERNEL<1, VS_> __VA_ARGS__;                                    \
-        else if (c->bs == 2) KERNEL<2, VS_> __VA_ARGS__;                               \
-        else KERNEL<3, VS_> __VA_ARGS__;                                               \
-    } while (0)
+// KERNEL<BS, MF> for the context's block size and operator form (MF = 1: element-factored)
 #define LAUNCH_BS(KERNEL, ...)                                                         \
     do {                                                                               \
-        if (c->elem) LAUNCH_VS(KERNEL, VS_ELEM, __VA_ARGS__);                          \
-        else if (c->sym) LAUNCH_VS(KERNEL, VS_SYM, __VA_ARGS__);                       \
-        else LAUNCH_VS(KERNEL, VS_FULL, __VA_ARGS__);                                  \
+        if (c->elem) {                                                                 \
+            if (c->bs == 1) KERNEL<1, 1> __VA_ARGS__;                                  \
+            else if (c->bs == 2) KERNEL<2, 1> __VA_ARGS__;                             \
+            else KERNEL<3, 1> __VA_ARGS__;                                             \
+        } else {                                                                       \
+            if (c->bs == 1) KERNEL<1, 0> __VA_ARGS__;                                  \
+            else if (c->bs == 2) KERNEL<2, 0> __VA_ARGS__;                             \
+            else KERNEL<3, 0> __VA_ARGS__;                                             \
+        }                                                                              \
     } while (0)
 
 #define KP_LIST(X) X(8) X(16) X(24) X(32) X(40) X(48) X(64)
 
 // Jacobi: y1 = omega D^-1 r on the fly (PRE = r1). Gauss-Seidel: y1 stored in s (PRE = 2) or 0.
-template <int BS, int VS>
+template <int BS, int MF>
 static void launch_smooth1(pod2g_ctx* c, Dims D, int want) {
     const int pre = c->smoother == POD2G_SMOOTHER_SGS ? (c->pre ? 2 : 0) : c->pre;
-    k_smooth1<BS, VS><<<D.G, POD2G_THREADS, 0, c->stream>>>(D, want, pre, c->d_row_ptr, c->d_col_idx,
+    k_smooth1<BS, MF><<<D.G, POD2G_THREADS, 0, c->stream>>>(D, want, pre, c->d_row_ptr, c->d_col_idx,
                                                              c->d_vals32, elem_op(c), c->d_dinv32, c->d_rdf,
                                                              c->d_s32, c->d_y32, c->d_part, c->d_sc);
 }
 
 // Gauss-Seidel sweep over all colours (forward from zero, or backward in place) on s.
-template <int BS, int VS>
+template <int BS, int MF>
 static int launch_gs(pod2g_ctx* c, Dims D, int want, int backward) {
     const ElemOp E = elem_op(c);
     for (int t = 0; t < c->ncolours; ++t) {
@@ -1070,12 +1058,12 @@ static int launch_gs(pod2g_ctx* c, Dims D, int want, int backward) {
         if (cnt == 0) continue;
         const int g = std::max(1, std::min(ceil_div((long long)cnt << D.lgBp, POD2G_THREADS), 8 * c->num_sms));
         if (backward)
-            k_gs<BS, VS, 1><<<g, POD2G_THREADS, 0, c->stream>>>(D, want, 0, col, c->d_cnodes + c->coff[col], cnt,
+            k_gs<BS, MF, 1><<<g, POD2G_THREADS, 0, c->stream>>>(D, want, 0, col, c->d_cnodes + c->coff[col], cnt,
                                                                  c->d_colour, c->d_row_ptr, c->d_col_idx,
                                                                  c->d_vals32, E, c->d_dinv32, c->d_rdf, c->d_s32,
                                                                  c->d_sc);
         else
-            k_gs<BS, VS, 0><<<g, POD2G_THREADS, 0, c->stream>>>(D, want, 1, col, c->d_cnodes + c->coff[col], cnt,
+            k_gs<BS, MF, 0><<<g, POD2G_THREADS, 0, c->stream>>>(D, want, 1, col, c->d_cnodes + c->coff[col], cnt,
                                                                  c->d_colour, c->d_row_ptr, c->d_col_idx,
                                                                  c->d_vals32, E, c->d_dinv32, c->d_rdf, c->d_s32,
                                                                  c->d_sc);
@@ -1163,19 +1151,19 @@ static void launch_prol(pod2g_ctx* c, Dims D, int want) {
 #undef PROL
 }
 
-template <int BS, int VS>
+template <int BS, int MF>
 static void launch_post(pod2g_ctx* c, Dims D, int want) {
     dim3 g(D.G), t(POD2G_THREADS);
     if (c->smoother == POD2G_SMOOTHER_SGS)  // s is final: only r^T s and beta
-        k_post<BS, 0, VS><<<g, t, 0, c->stream>>>(D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, elem_op(c),
+        k_post<BS, 0, MF><<<g, t, 0, c->stream>>>(D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, elem_op(c),
                                                   c->d_dinv32, c->d_rdf, c->d_s32, c->d_s32, c->d_part,
                                                   c->d_counters + CNT_POST, c->d_sc);
     else if (c->post)
-        k_post<BS, 1, VS><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
+        k_post<BS, 1, MF><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
                                                   elem_op(c), c->d_dinv32, c->d_rdf, c->d_y32, c->d_s32, c->d_part,
                                                   c->d_counters + CNT_POST, c->d_sc);
     else
-        k_post<BS, 0, VS><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
+        k_post<BS, 0, MF><<<g, t, 0, c->stream>>>(D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32,
                                                   elem_op(c), c->d_dinv32, c->d_rdf, c->d_y32, c->d_s32, c->d_part,
                                                   c->d_counters + CNT_POST, c->d_sc);
 }

@@ -76,11 +76,6 @@ struct pod2g_ctx {
     float* d_phi32 = nullptr;           // mixed paths (BF16-rounded values for MIXED_BF16PHI)
     __nv_bfloat16* d_phi16 = nullptr;   // MIXED_BF16PHI: the basis as stored BF16
 
-    // symmetric storage of the assembled values (sym = 1): upper blocks only
-    int sym = 0, nnzb_up = 0;
-    int32_t* d_upidx = nullptr;         // [nnzb] upper-store index of each block, SYM_T if transposed
-    int32_t* d_upfull = nullptr;        // [nnzb_up] full-pattern index of each stored block
-
     // element-factored operator (pod2g_create_elements; elem = 1)
     int elem = 0, n_el = 0, npe = 0;
     uint64_t* d_desc = nullptr;         // [nnzb] block descriptors (see ElemOp)
@@ -286,15 +281,7 @@ struct ElemOp {
     const float* coef;        // [n_el][Bp]
     const float* kref;        // [npe*npe][bs*bs]
     int nk;                   // floats in kref
-    const int32_t* upidx;     // symmetric storage: [nnzb] upper-store block of each block (| SYM_T if transposed)
 };
-
-// Symmetric storage of the assembled FP32 values (structurally symmetric patterns):
-// only blocks (i, j >= i) are stored; block (i, j < i) is the transpose of stored (j, i).
-#define SYM_T 0x80000000u
-
-// value source of the sparse row kernels
-enum { VS_FULL = 0, VS_ELEM = 1, VS_SYM = 2 };
 
 static inline ElemOp elem_op(const pod2g_ctx* c) {
     ElemOp E;
@@ -303,7 +290,6 @@ static inline ElemOp elem_op(const pod2g_ctx* c) {
     E.coef = c->d_coef32;
     E.kref = c->d_kref32;
     E.nk = c->npe * c->npe * c->bs * c->bs;
-    E.upidx = c->d_upidx;
     return E;
 }
 

@@ -25,31 +25,6 @@ __global__ void k_convert_values(const double* __restrict__ v64, float* __restri
     }
 }
 
-// Symmetric storage: the FP32 values of one instance, every block (i, j < i) taken
-// as the transpose of the stored block (j, i): the contiguous staging copy is the
-// mirrored matrix the kernels apply, and the slot's lane of the upper store is written.
-template <int BS>
-__global__ void k_convert_values_sym(const double* __restrict__ v64, const int32_t* __restrict__ upidx,
-                                     const int32_t* __restrict__ upfull, float* __restrict__ v32_stage,
-                                     float* __restrict__ vals32, long long nnzb, int Bp, int slot) {
-    const long long total = nnzb * BS * BS;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long blk = e / (BS * BS);
-        const int rc = (int)(e - blk * BS * BS), r = rc / BS, cc = rc % BS;
-        const uint32_t ui = (uint32_t)upidx[blk];
-        const long long u = ui & ~SYM_T;
-        float v;
-        if (ui & SYM_T) {
-            v = __double2float_rn(v64[(long long)upfull[u] * BS * BS + cc * BS + r]);
-        } else {
-            v = __double2float_rn(v64[e]);
-            vals32[(u * BS * BS + rc) * Bp + slot] = v;
-        }
-        v32_stage[e] = v;
-    }
-}
-
 // D^{-1}: one thread per unknown. status[0] set to NOT_SPD on a non-positive or
 // non-finite diagonal entry.
 template <typename V>
@@ -315,17 +290,7 @@ int setup_values(pod2g_ctx* c, int slot, const double* vals_dev) {
         }
     } else {
         int g = std::min(ceil_div(total, T), 8 * c->num_sms);
-        if (!c->sym)
-            k_convert_values<<<g, T, 0, c->stream>>>(vals_dev, c->d_stage32, c->d_vals32, total, c->Bp, slot);
-        else if (c->bs == 1)
-            k_convert_values_sym<1><<<g, T, 0, c->stream>>>(vals_dev, c->d_upidx, c->d_upfull, c->d_stage32,
-                                                            c->d_vals32, c->nnzb, c->Bp, slot);
-        else if (c->bs == 2)
-            k_convert_values_sym<2><<<g, T, 0, c->stream>>>(vals_dev, c->d_upidx, c->d_upfull, c->d_stage32,
-                                                            c->d_vals32, c->nnzb, c->Bp, slot);
-        else
-            k_convert_values_sym<3><<<g, T, 0, c->stream>>>(vals_dev, c->d_upidx, c->d_upfull, c->d_stage32,
-                                                            c->d_vals32, c->nnzb, c->Bp, slot);
+        k_convert_values<<<g, T, 0, c->stream>>>(vals_dev, c->d_stage32, c->d_vals32, total, c->Bp, slot);
         P2G_TRY(pod2g_check_launch(c));
         P2G_TRY(setup_from_stage32(c, slot, st));
     }

@@ -30,27 +30,3 @@ def round_phi(phi, phi_dtype: str) -> np.ndarray:
     if phi_dtype == "bf16":
         return round_bf16(phi)
     raise ValueError(phi_dtype)
-
-
-def mirror_upper(row_ptr, col_idx, values) -> np.ndarray:
-    """Block values with every block (i, j < i) replaced by the transpose of block (j, i).
-
-    The mixed-precision solver stores only the blocks on and above the diagonal of a
-    structurally symmetric pattern; an assembled K is symmetric only up to FP64
-    rounding, so the system it solves is the rounded upper triangle mirrored."""
-    v = np.array(values, dtype=np.float64)
-    nb = len(row_ptr) - 1
-    rows = np.repeat(np.arange(nb, dtype=np.int64), np.diff(row_ptr))
-    cols = np.asarray(col_idx, dtype=np.int64)
-    keys = rows * nb + cols                       # ascending (CSR, sorted columns)
-    lower = np.nonzero(cols < rows)[0]
-    src = np.searchsorted(keys, cols[lower] * nb + rows[lower])
-    assert np.array_equal(keys[src], cols[lower] * nb + rows[lower]), "pattern is not structurally symmetric"
-    if lower.size:
-        v[lower] = np.transpose(v[src], (0, 2, 1))
-    return v
-
-
-def round_f32_sym(row_ptr, col_idx, values) -> np.ndarray:
-    """The FP32 matrix the mixed path solves for assembled values [nnzb, bs, bs]."""
-    return mirror_upper(row_ptr, col_idx, round_f32(values))

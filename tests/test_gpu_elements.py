@@ -88,10 +88,8 @@ def test_element_batch_dev_setup_and_memory(pkg):
     X = torch.empty_like(B)
     se = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, elements=_elements(P), max_batch=64, omega=wl.spec.omega)
     sa = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, max_batch=64, omega=wl.spec.omega)
-    # the element context holds no per-slot matrix values (the assembled one stores the
-    # blocks on and above the diagonal of its symmetric pattern)
-    rows = np.repeat(np.arange(P.n_nodes), np.diff(P.row_ptr))
-    values_bytes = int(np.sum(P.col_idx >= rows)) * P.bs * P.bs * 64 * 4
+    # the element context holds no per-slot matrix values
+    values_bytes = P.nnzb * P.bs * P.bs * 64 * 4
     assert sa.device_bytes() - se.device_bytes() >= 0.9 * values_bytes
     st, sts = se.set_coeffs_batch_dev(list(range(m)), C)
     assert st == pkg.OK and np.all(sts == pkg.OK)

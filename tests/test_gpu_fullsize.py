@@ -18,7 +18,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 from oracle import pod2g_oracle as O  # noqa: E402
 from synth.problems import Workload  # noqa: E402
-from synth.rounding import round_f32_sym, round_phi  # noqa: E402
+from synth.rounding import round_f32, round_phi  # noqa: E402
 from synth.snapshots import pod_basis  # noqa: E402
 
 TOL = 1e-8
@@ -57,7 +57,7 @@ def _run_batch(pkg, name, sample):
     X = x.cpu().numpy()
     bh = b.cpu().numpy()
     for i in range(B):
-        v = round_f32_sym(P.row_ptr, P.col_idx, vals[i].cpu().numpy().reshape(-1, P.bs, P.bs))
+        v = round_f32(vals[i].cpu().numpy()).reshape(-1, P.bs, P.bs)
         K = P.csr(v)
         bn = np.linalg.norm(bh[i])
         true_rel = np.linalg.norm(bh[i] - K @ X[i]) / bn
@@ -69,7 +69,7 @@ def _run_batch(pkg, name, sample):
         assert abs(true_rel - rel[i]) <= bound + 1e-3 * true_rel, (i, true_rel, rel[i], bound)
     phi_used = round_phi(Phi, wl.spec.phi_dtype)
     for i in sample:
-        K = P.csr(round_f32_sym(P.row_ptr, P.col_idx, vals[i].cpu().numpy().reshape(-1, P.bs, P.bs)))
+        K = P.csr(round_f32(vals[i].cpu().numpy()).reshape(-1, P.bs, P.bs))
         ref = O.pod2g_pcg(K, bh[i], None, phi_used, wl.spec.omega, TOL, 5000)
         print(f"instance {i}: gpu iters {iters[i]} oracle iters {ref.iters}; oracle history tail "
               f"{[f'{h:.3e}' for h in ref.history[-40:]]}")

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import pod2g_oracle as O  # noqa: E402
 from synth.problems import Workload  # noqa: E402
-from synth.rounding import round_f32, round_f32_sym, round_phi  # noqa: E402
+from synth.rounding import round_f32, round_phi  # noqa: E402
 from synth.snapshots import pod_basis  # noqa: E402
 
 TOL = 1e-8
@@ -73,7 +73,7 @@ def test_mixed_batched_matches_oracle(pkg, name, precision):
     Bm = wl.rhs(m)
     phi_used = round_phi(Phi, "bf16" if precision == pkg.MIXED_BF16PHI else "f32")
     s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=precision, omega=wl.spec.omega, max_batch=m)
-    vals = [round_f32_sym(P.row_ptr, P.col_idx, wl.values(xi)) for xi in xis]
+    vals = [round_f32(wl.values(xi)) for xi in xis]
     for i in range(m):
         assert s.set_values(i, vals[i]) == pkg.OK
     X, iters, rel, st, rc = s.solve_batch(list(range(m)), Bm, tol=TOL, maxit=3000)

@@ -210,18 +210,3 @@ def test_batched_torch_assembly_identical(name):
     V = wl.values_torch(xis).numpy()
     for i, xi in enumerate(xis):
         assert np.array_equal(V[i], wl.values(xi))
-
-
-def test_mirror_upper_makes_blocks_symmetric():
-    from synth.rounding import mirror_upper, round_f32, round_f32_sym
-    P = fe._build("q4", 4)
-    c = np.random.default_rng(7).lognormal(0, 0.3, P.n_el)
-    v = P.values(c)
-    m = mirror_upper(P.row_ptr, P.col_idx, v)
-    K = P.csr(m).toarray()
-    assert np.array_equal(K, K.T)
-    rows = np.repeat(np.arange(P.n_nodes), np.diff(P.row_ptr))
-    up = P.col_idx >= rows
-    assert np.array_equal(m[up], v[up])               # blocks on and above the diagonal untouched
-    assert np.allclose(m, v, rtol=1e-14, atol=1e-14 * np.abs(v).max())
-    assert np.array_equal(round_f32_sym(P.row_ptr, P.col_idx, v), mirror_upper(P.row_ptr, P.col_idx, round_f32(v)))
