@@ -115,6 +115,10 @@ static void free_all(pod2g_ctx* c) {
     if (c->h_scal64) cudaFreeHost(c->h_scal64);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_sc2) cudaFreeHost(c->h_sc2);
+    if (c->h_err2) cudaFreeHost(c->h_err2);
+    for (auto ev : c->la_ev)
+        if (ev) cudaEventDestroy(ev);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     for (auto ev : c->tev) cudaEventDestroy(ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -361,6 +365,16 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
         *c->h_err = 0;
         if (cudaMallocHost(&c->h_sc, sizeof(SlotScalars) * Bp) != cudaSuccess) { free_all(c); delete c; return POD2G_OOM; }
         std::memset(c->h_sc, 0, sizeof(SlotScalars) * Bp);
+        if (cudaMallocHost(&c->h_sc2, sizeof(SlotScalars) * Bp) != cudaSuccess ||
+            cudaMallocHost(&c->h_err2, sizeof(int)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->la_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->la_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+            free_all(c);
+            delete c;
+            return POD2G_OOM;
+        }
+        std::memset(c->h_sc2, 0, sizeof(SlotScalars) * Bp);
+        *c->h_err2 = 0;
         if (batched_alloc(c) != POD2G_OK) { free_all(c); delete c; return POD2G_INVALID_ARG; }
     }
     c->setup_ok.assign(c->B, 0);

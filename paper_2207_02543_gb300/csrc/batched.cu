@@ -41,6 +41,7 @@
 #include <cooperative_groups.h>
 
 #include <chrono>
+#include <cstring>
 #include <cmath>
 
 namespace cg = cooperative_groups;
@@ -1365,12 +1366,46 @@ int batched_run(pod2g_ctx* c, const std::vector<int>& lanes) {
     int64_t bound = 2;
     for (int b : lanes) bound = std::max<int64_t>(bound, (int64_t)c->h_sc[b].maxit / c->chunk + 2);
     if (c->spin_limit > 0) bound = std::min<int64_t>(bound, c->spin_limit);
-    for (int64_t polls = 0;; ++polls) {
-        bool all = true;
-        for (int b : lanes) all = all && c->h_sc[b].state == SLOT_DONE;
-        if (all) return POD2G_OK;
-        if (polls >= bound) return POD2G_TIMEOUT;
-        P2G_TRY(batched_chunk(c));
+    auto all_done = [&](const SlotScalars* hs) {
+        for (int b : lanes)
+            if (hs[b].state != SLOT_DONE) return false;
+        return true;
+    };
+    if (c->timing || !c->h_sc2) {
+        for (int64_t polls = 0;; ++polls) {
+            if (all_done(c->h_sc)) return POD2G_OK;
+            if (polls >= bound) return POD2G_TIMEOUT;
+            P2G_TRY(batched_chunk(c));
+        }
+    }
+    // One chunk of lookahead: launch k + 1 is queued before the lane states after
+    // launch k are examined, so the GPU does not idle during the host's check. Lanes
+    // that finished are frozen on the device, so the extra launch changes nothing.
+    if (all_done(c->h_sc)) return POD2G_OK;
+    SlotScalars* hb[2] = {c->h_sc, c->h_sc2};
+    int* he[2] = {c->h_err, c->h_err2};
+    auto enqueue = [&](int64_t k) -> int {
+        P2G_TRY(build_graph(c));
+        P2G_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+        c->launches += c->iter_launches * c->chunk;
+        P2G_CUDA(cudaMemcpyAsync(hb[k & 1], c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
+        P2G_CUDA(cudaMemcpyAsync(he[k & 1], c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        P2G_CUDA(cudaEventRecord(c->la_ev[k & 1], c->stream));
+        return POD2G_OK;
+    };
+    P2G_TRY(enqueue(0));
+    for (int64_t k = 0;; ++k) {
+        const bool ahead = k + 1 < bound;
+        if (ahead) P2G_TRY(enqueue(k + 1));
+        P2G_CUDA(cudaEventSynchronize(c->la_ev[k & 1]));
+        const bool err = *he[k & 1] != 0, done = all_done(hb[k & 1]);
+        if (err || done || !ahead) {
+            P2G_CUDA(cudaStreamSynchronize(c->stream));
+            const int64_t last = ahead ? k + 1 : k;   // the latest copy holds the final states
+            if (hb[last & 1] != c->h_sc) std::memcpy(c->h_sc, hb[last & 1], sizeof(SlotScalars) * c->Bp);
+            if (err || *he[last & 1]) return POD2G_TIMEOUT;
+            return done ? POD2G_OK : POD2G_TIMEOUT;
+        }
     }
 }
 

@@ -123,6 +123,9 @@ struct pod2g_ctx {
     SlotScalars* h_sc = nullptr;        // pinned host mirror
     int* d_err = nullptr;               // device error word: set when a bounded device wait expires
     int* h_err = nullptr;               // pinned host mirror
+    SlotScalars* h_sc2 = nullptr;       // second pinned mirror and error word for the lookahead launch
+    int* h_err2 = nullptr;
+    cudaEvent_t la_ev[2] = {nullptr, nullptr};
     int* d_mask = nullptr;              // [2 Bp] lane mask and slot list for load / finalize
     double* d_iob = nullptr;            // [B][n] staging of right-hand sides (host-buffer entry points)
     double* d_iox = nullptr;            // [B][n] staging of x0 / x
