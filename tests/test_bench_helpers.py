@@ -1,0 +1,39 @@
+"""Host logic of the benchmark (no GPU): metric naming, workload description and the
+algorithmic-byte model the roofline fraction is computed from."""
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+from synth.problems import Workload  # noqa: E402
+
+
+def test_metric_and_workload_names():
+    assert bench.fmt_tol(1e-8) == "1e-8" and bench.fmt_tol(1e-4) == "1e-4"
+    assert bench.method_name("pcg") == "POD-2G-PCG"
+    d = bench.workload_desc(Workload("q4_512"), 64, 1e-8)
+    assert "526,338 dofs" in d and "512x512" in d and "batch 64" in d and "tol 1e-8" in d
+
+
+def test_kernel_bytes_model():
+    wl = Workload("q4_512")
+    P = wl.problem
+    kb = bench.kernel_bytes(wl, 24, lane_iters=64, launches=1, G=1216, Bp=64)
+    vals = P.nnzb * 4 * 4
+    # one launch with 64 active instances: values + p + q (double-float) + pattern
+    assert kb["k_spmv"] == 64 * (vals + 16 * P.n) + P.nnzb * 4 + (P.n_nodes + 1) * 4
+    assert kb["k_upd"] == 64 * 48 * P.n
+    assert kb["k_restrict"] == 64 * 4 * P.n + P.n * 24 * 4
+    # the element form replaces the per-instance values by one coefficient per element
+    ke = bench.kernel_bytes(wl, 24, 64, 1, 1216, 64, elements=True)
+    assert ke["k_spmv"] - kb["k_spmv"] == 64 * (P.n_el * 4 - vals) + P.nnzb * 8 + P.n_nodes * 32
+    # Gauss-Seidel groups: two value passes before the coarse correction, one after
+    ks = bench.kernel_bytes(wl, 24, 64, 1, 1216, 64, sgs=True)
+    assert ks["k_smooth1"] > 1.9 * kb["k_smooth1"] and ks["k_prol"] < kb["k_prol"]
+
+
+def test_measured_peak_fallback(tmp_path, monkeypatch):
+    peaks, kind = bench.measured_peaks()
+    assert kind in ("measured", "fallback") and peaks["hbm_gbs"] > 1000
