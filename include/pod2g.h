@@ -9,7 +9,9 @@
  *     y  <- 0;  r1 damped-Jacobi sweeps  y <- y + omega D^{-1} (r - K y)
  *     e_c = (Phi^T K Phi)^{-1} Phi^T (r - K y);   y <- y + Phi e_c
  *     r2 damped-Jacobi sweeps;                    s = y
- * with D = diag(K). The outer iteration is Algorithm 1 with T^{-1} r := s.
+ * with D = diag(K) (or forward / backward multicolour Gauss-Seidel sweeps, see
+ * pod2g_opts.smoother). The outer iteration is Algorithm 1 with T^{-1} r := s,
+ * or, as the stationary method, u <- u + s(f - K u) (Algorithm 2 iterated).
  *
  * Conventions
  *   - n_brows block rows of size bs (1, 2 or 3); n = n_brows * bs unknowns.
@@ -31,11 +33,12 @@
  *                           checked on the host every iteration (the plain path);
  *       POD2G_MIXED_FP32PHI batched path: values stored in FP32 (the system solved
  *                           is the one with FP32-rounded values), preconditioner
- *                           (smoothing, restriction, prolongation, K_c build) in
- *                           FP32 with FP32 Phi, outer recurrences (x, r, p, K p,
- *                           dot products) in double-float (~48-bit significand,
- *                           pairs of FP32, error-free transformations), scalars
- *                           and the k x k Cholesky factor in FP64;
+ *                           (smoothing, restriction, prolongation) in FP32 with
+ *                           FP32 Phi, K_c = Phi^T (K Phi) formed in double-float,
+ *                           outer recurrences (x, r, p, K p, dot products) in
+ *                           double-float (~48-bit significand, pairs of FP32,
+ *                           error-free transformations), scalars and the k x k
+ *                           Cholesky factor in FP64;
  *       POD2G_MIXED_BF16PHI as above with Phi rounded to BF16.
  *   - Ownership: the library copies every input; callers keep their buffers.
  *     Output buffers belong to the caller. Functions whose name ends in _dev take
