@@ -53,3 +53,15 @@ def test_host_only_calls(lib):
     assert lib.pod2g_info(None, None, None, None, None) == pkg.INVALID_ARG
     assert lib.pod2g_launch_count(None) == 0
     lib.pod2g_destroy(None)
+
+
+def test_opts_struct_layout_matches(lib):
+    """pod2g_default_opts fills exactly sizeof(pod2g_opts) bytes: a sentinel placed right
+    after the binding's struct must survive, and the appended fields read back their defaults."""
+    import paper_2207_02543_gb300 as pkg
+    size = ctypes.sizeof(pkg.Opts)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    lib.pod2g_default_opts(ctypes.cast(buf, ctypes.POINTER(pkg.Opts)))
+    assert all(b == 0xAB for b in bytes(buf)[size:])
+    o = ctypes.cast(buf, ctypes.POINTER(pkg.Opts)).contents
+    assert o.method == pkg.PCG and o.smoother == pkg.SMOOTHER_JACOBI and o.precision == pkg.MIXED_FP32PHI
