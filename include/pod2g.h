@@ -180,6 +180,22 @@ int pod2g_set_coeffs(pod2g_t ctx, int slot, const double* coeffs, int on_device)
 int pod2g_set_coeffs_batch_dev(pod2g_t ctx, int nslots, const int* slots,
                                const double* coeffs_dev, int* status);
 
+/* Element contexts: a registered parametrization of the element coefficients,
+ *     c_e(theta) = exp(mu + sigma * sum_j modes[e][j] * theta_j)   (lognormal != 0)
+ *     c_e(theta) = mu + sigma * sum_j modes[e][j] * theta_j        (lognormal == 0),
+ * the form of a truncated Karhunen-Loeve expansion of the material field evaluated
+ * at the elements (the paper's random material properties, Section 4.1, Section 4.2).
+ * modes: host [n_elems][m] doubles (copied), 1 <= m <= 64. */
+int pod2g_set_field(pod2g_t ctx, const double* modes, int m, double mu, double sigma, int lognormal);
+
+/* Instance set-up from the parameters theta (host, m doubles): c_e(theta) is
+ * evaluated on the device (FP64, then rounded to FP32 like pod2g_set_coeffs), then
+ * the set-up of pod2g_set_coeffs. A non-finite c_e gives POD2G_NONFINITE, c_e <= 0
+ * POD2G_NOT_SPD. POD2G_INVALID_ARG without a registered field. */
+int pod2g_set_theta(pod2g_t ctx, int slot, const double* theta);
+/* Several slots: theta holds nslots * m doubles (host). */
+int pod2g_set_theta_batch(pod2g_t ctx, int nslots, const int* slots, const double* theta, int* status);
+
 /* Solve one instance (Algorithm 3). b, x0 (NULL: zero) and x are host arrays of
  * n doubles. iters / relres may be NULL. */
 int pod2g_solve(pod2g_t ctx, int slot, const double* b, const double* x0, double tol,
@@ -224,6 +240,10 @@ int pod2g_submit(pod2g_t ctx, const double* values, const double* b, const doubl
 int pod2g_poll(pod2g_t ctx, uint64_t ticket, double* x, int* iters, double* relres,
                int* status, double* latency_s);
 int pod2g_serve_stop(pod2g_t ctx);
+/* Serving by parameters (element contexts with a registered field): a request
+ * carries theta (host, m doubles) instead of coefficients; otherwise as pod2g_submit. */
+int pod2g_submit_theta(pod2g_t ctx, const double* theta, const double* b, const double* x0,
+                       double tol, int maxit, uint64_t* ticket);
 
 /* Query sizes: n, nnzb, k, max_batch (any pointer may be NULL). */
 int pod2g_info(pod2g_t ctx, int* n, int* nnzb, int* k, int* max_batch);

@@ -26,7 +26,7 @@ EXPORTS = [
     "pod2g_serve_stop", "pod2g_info", "pod2g_launch_count", "pod2g_kernel_timing", "pod2g_kernel_times",
     "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc", "pod2g_device_bytes", "pod2g_create_elements",
     "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev", "pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune",
-    "pod2g_rom_solution_dev",
+    "pod2g_rom_solution_dev", "pod2g_set_field", "pod2g_set_theta", "pod2g_set_theta_batch", "pod2g_submit_theta",
 ]
 NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
 TOO_LARGE = 11
@@ -77,6 +77,10 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_set_coeffs.argtypes = [P, I, P, I]
     lib.pod2g_get_tuning.argtypes = [P, C.POINTER(Tuning)]
     lib.pod2g_rom_solution_dev.argtypes = [P, I, IP, P, P]
+    lib.pod2g_set_field.argtypes = [P, DP, I, D, D, I]
+    lib.pod2g_set_theta.argtypes = [P, I, DP]
+    lib.pod2g_set_theta_batch.argtypes = [P, I, IP, DP, IP]
+    lib.pod2g_submit_theta.argtypes = [P, DP, DP, DP, D, I, C.POINTER(C.c_uint64)]
     lib.pod2g_set_tuning.argtypes = [P, C.POINTER(Tuning)]
     lib.pod2g_autotune.argtypes = [P, I, IP, P, I, C.POINTER(Tuning)]
     lib.pod2g_set_coeffs_batch_dev.argtypes = [P, I, IP, P, IP]
@@ -105,7 +109,8 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_destroy.restype = None
     lib.pod2g_strerror.argtypes = [I]
     lib.pod2g_strerror.restype = C.c_char_p
-    for name in ("pod2g_rom_solution_dev", "pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune", "pod2g_create", "pod2g_create_elements", "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
+    for name in ("pod2g_set_field", "pod2g_set_theta", "pod2g_set_theta_batch", "pod2g_submit_theta",
+                 "pod2g_rom_solution_dev", "pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune", "pod2g_create", "pod2g_create_elements", "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev",
                  "pod2g_set_values", "pod2g_set_values_batch_dev", "pod2g_solve",
                  "pod2g_solve_batch", "pod2g_solve_batch_dev", "pod2g_serve_start", "pod2g_submit", "pod2g_poll",
                  "pod2g_serve_stop", "pod2g_info"):
@@ -272,6 +277,42 @@ class Solver:
         if v.size != self.inst_len:
             return INVALID_ARG
         return self._lib.pod2g_set_coeffs(self.h, slot, v.ctypes.data_as(C.c_void_p), 0)
+
+    def set_field(self, modes, mu=0.0, sigma=1.0, lognormal=True) -> int:
+        """Element contexts: c_e(theta) = exp(mu + sigma * modes[e] . theta) (or without exp).
+        modes: [n_elems, m] float64 (host)."""
+        modes = np.ascontiguousarray(modes, dtype=np.float64)
+        if modes.ndim != 2 or modes.shape[0] != self.inst_len:
+            return INVALID_ARG
+        self.field_m = modes.shape[1]
+        return self._lib.pod2g_set_field(self.h, _dptr(modes), modes.shape[1], mu, sigma, int(lognormal))
+
+    def set_theta(self, slot: int, theta) -> int:
+        t = _f64(theta).reshape(-1)
+        if t.size != getattr(self, "field_m", -1):
+            return INVALID_ARG
+        return self._lib.pod2g_set_theta(self.h, slot, _dptr(t))
+
+    def set_theta_batch(self, slots, thetas):
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        t = _f64(thetas).reshape(-1)
+        status = np.zeros(len(slots), dtype=np.int32)
+        if t.size != len(slots) * getattr(self, "field_m", -1):
+            return INVALID_ARG, status
+        st = self._lib.pod2g_set_theta_batch(self.h, len(slots), slots.ctypes.data_as(C.POINTER(C.c_int)), _dptr(t),
+                                             status.ctypes.data_as(C.POINTER(C.c_int)))
+        return st, status
+
+    def submit_theta(self, theta, b, x0=None, tol=1e-8, maxit=1000):
+        t = _f64(theta).reshape(-1)
+        b = _f64(b)
+        if t.size != getattr(self, "field_m", -1) or b.size != self.n or (x0 is not None and np.size(x0) != self.n):
+            return INVALID_ARG, 0
+        x0a = _f64(x0) if x0 is not None else None
+        tk = C.c_uint64(0)
+        st = self._lib.pod2g_submit_theta(self.h, _dptr(t), _dptr(b), _dptr(x0a) if x0a is not None else None, tol,
+                                          maxit, C.byref(tk))
+        return st, tk.value
 
     def set_coeffs_batch_dev(self, slots, coeffs_dev):
         """coeffs_dev: CUDA float64 tensor [len(slots), n_elems]."""

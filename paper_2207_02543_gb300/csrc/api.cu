@@ -109,7 +109,7 @@ static void free_all(pod2g_ctx* c) {
                     c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
                     c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
                     c->d_pdf, c->d_qdf, c->d_bdf, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
-                    c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32, c->d_cnodes, c->d_colour};
+                    c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32, c->d_cnodes, c->d_colour, c->d_modes, c->d_theta};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_scal64) cudaFreeHost(c->h_scal64);
@@ -550,6 +550,59 @@ int pod2g_set_coeffs_batch_dev(pod2g_t c, int nslots, const int* slots, const do
         P2G_TRY(setup_coeffs(c, slots[i], coeffs_dev + (size_t)i * c->n_el));
     }
     return finish_setup(c, nslots, slots, status);
+}
+
+int pod2g_set_field(pod2g_t c, const double* modes, int m, double mu, double sigma, int lognormal) {
+    if (!c || !modes || !c->elem || c->serving || m < 1 || m > 64) return POD2G_INVALID_ARG;
+    if (!std::isfinite(mu) || !std::isfinite(sigma)) return POD2G_NONFINITE;
+    for (long long t = 0; t < (long long)c->n_el * m; ++t)
+        if (!std::isfinite(modes[t])) return POD2G_NONFINITE;
+    if (c->d_modes) {  // replace an earlier field
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_modes);
+        cudaFree(c->d_theta);
+        c->d_modes = c->d_theta = nullptr;
+        c->allocated -= ((sizeof(double) * (size_t)c->n_el * c->field_m + 255) & ~(size_t)255) +
+                        ((sizeof(double) * (size_t)c->B * c->field_m + 255) & ~(size_t)255);
+        c->field_m = 0;
+    }
+    int st = dev_alloc(c, (void**)&c->d_modes, sizeof(double) * (size_t)c->n_el * m);
+    if (st == POD2G_OK) st = dev_alloc(c, (void**)&c->d_theta, sizeof(double) * (size_t)c->B * m);
+    if (st != POD2G_OK) {
+        if (c->d_modes) {
+            cudaFree(c->d_modes);
+            c->allocated -= (sizeof(double) * (size_t)c->n_el * m + 255) & ~(size_t)255;
+        }
+        c->d_modes = nullptr;
+        return st;
+    }
+    P2G_CUDA(cudaMemcpy(c->d_modes, modes, sizeof(double) * (size_t)c->n_el * m, cudaMemcpyHostToDevice));
+    c->field_m = m;
+    c->field_mu = mu;
+    c->field_sigma = sigma;
+    c->field_log = lognormal ? 1 : 0;
+    return POD2G_OK;
+}
+
+int pod2g_set_theta_batch(pod2g_t c, int nslots, const int* slots, const double* theta, int* status) {
+    if (!c || !slots || !theta || nslots < 1 || nslots > c->B) return POD2G_INVALID_ARG;
+    if (c->serving || !c->elem || c->field_m == 0) return POD2G_INVALID_ARG;
+    for (int i = 0; i < nslots; ++i)
+        if (slots[i] < 0 || slots[i] >= c->B) return POD2G_INVALID_ARG;
+    const int m = c->field_m;
+    P2G_CUDA(cudaMemcpyAsync(c->d_theta, theta, sizeof(double) * (size_t)nslots * m, cudaMemcpyHostToDevice,
+                             c->stream));
+    for (int i = 0; i < nslots; ++i) {
+        c->setup_ok[slots[i]] = 0;
+        P2G_TRY(setup_theta(c, slots[i], c->d_theta + (size_t)i * m));
+    }
+    return finish_setup(c, nslots, slots, status);
+}
+
+int pod2g_set_theta(pod2g_t c, int slot, const double* theta) {
+    int st = POD2G_OK;
+    int rc = pod2g_set_theta_batch(c, 1, &slot, theta, &st);
+    return rc;
 }
 
 int pod2g_set_values_batch_dev(pod2g_t c, int nslots, const int* slots, const double* values_dev, int* status) {

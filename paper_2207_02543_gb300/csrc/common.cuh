@@ -82,6 +82,11 @@ struct pod2g_ctx {
     int32_t* d_rowel = nullptr;         // [nb][POD2G_ELEM_RE] adjacent elements, ascending, -1 padded
     float* d_kref32 = nullptr;          // [npe*npe][bs*bs] FP32 reference sub-blocks
     float* d_coef32 = nullptr;          // [n_el][Bp] FP32 coefficients, slot-interleaved
+    // parametrized coefficients c_e(theta) (pod2g_set_field)
+    int field_m = 0, field_log = 1;
+    double field_mu = 0.0, field_sigma = 1.0;
+    double* d_modes = nullptr;          // [n_el][m]
+    double* d_theta = nullptr;          // [B][m] staging of parameter vectors
 
     // per-slot set-up results
     double* d_Lc = nullptr;             // [B][k][k] Cholesky factors (FP64)
@@ -157,8 +162,9 @@ struct pod2g_ctx {
 
 struct ServeRequest {
     uint64_t ticket;
-    std::vector<double> values, b, x0, x;
+    std::vector<double> values, b, x0, x;   // values: block values, coefficients, or theta
     bool has_x0 = false;
+    bool theta = false;                     // values holds the parameters theta
     double tol = 1e-8;
     int maxit = 1000;
     int iters = 0, status = POD2G_PENDING;
@@ -335,6 +341,7 @@ int plain_solve(pod2g_ctx* c, int slot, const double* b_dev, const double* x0_de
                 double* x_dev, int* iters, double* relres, int* status);
 int setup_values(pod2g_ctx* c, int slot, const double* vals_dev);
 int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev);
+int setup_theta(pod2g_ctx* c, int slot, const double* theta_dev);
 // doubles describing one instance: matrix values, or element coefficients
 static inline size_t instance_len(const pod2g_ctx* c) {
     return c->elem ? (size_t)c->n_el : (size_t)c->nnzb * c->bs * c->bs;

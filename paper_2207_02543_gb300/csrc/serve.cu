@@ -93,8 +93,16 @@ static void worker_main(pod2g_ctx* c) {
             for (size_t i = 0; i < joining.size() && fatal == POD2G_OK; ++i) {
                 ServeRequest* r = joining[i];
                 int b = jl[i];
-                if (cudaMemcpyAsync(c->d_stage, r->values.data(), vb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-                    setup_instance(c, b, c->d_stage) != POD2G_OK) {
+                const bool ok_setup =
+                    r->theta
+                        ? cudaMemcpyAsync(c->d_theta + (size_t)b * c->field_m, r->values.data(),
+                                          sizeof(double) * c->field_m, cudaMemcpyHostToDevice, c->stream) ==
+                                  cudaSuccess &&
+                              setup_theta(c, b, c->d_theta + (size_t)b * c->field_m) == POD2G_OK
+                        : cudaMemcpyAsync(c->d_stage, r->values.data(), vb, cudaMemcpyHostToDevice, c->stream) ==
+                                  cudaSuccess &&
+                              setup_instance(c, b, c->d_stage) == POD2G_OK;
+                if (!ok_setup) {
                     fatal = POD2G_CUDA_ERROR;
                     break;
                 }
@@ -196,6 +204,34 @@ int pod2g_submit(pod2g_t c, const double* values, const double* b, const double*
     }
     ServeRequest* r = new ServeRequest();
     r->values.assign(values, values + nv);
+    r->b.assign(b, b + n);
+    if (x0) { r->x0.assign(x0, x0 + n); r->has_x0 = true; }
+    r->tol = tol;
+    r->maxit = maxit;
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        r->ticket = c->next_ticket++;
+        *ticket = r->ticket;
+        c->queue.push_back(r);
+    }
+    c->cv.notify_one();
+    return POD2G_OK;
+}
+
+int pod2g_submit_theta(pod2g_t c, const double* theta, const double* b, const double* x0, double tol, int maxit,
+                       uint64_t* ticket) {
+    if (!c || !theta || !b || !ticket || !(tol >= 0.0) || maxit < 0) return POD2G_INVALID_ARG;
+    if (!c->elem || c->field_m == 0) return POD2G_INVALID_ARG;
+    const size_t n = c->n;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        if (!c->serving) return POD2G_INVALID_ARG;
+        if ((int)c->queue.size() >= c->max_queue) return POD2G_ADMISSION;
+    }
+    ServeRequest* r = new ServeRequest();
+    r->values.assign(theta, theta + c->field_m);
+    r->theta = true;
     r->b.assign(b, b + n);
     if (x0) { r->x0.assign(x0, x0 + n); r->has_x0 = true; }
     r->tol = tol;

@@ -93,6 +93,22 @@ __global__ void k_coef_convert(const double* __restrict__ c64, float* __restrict
     }
 }
 
+// Parametrized coefficients of one instance: c_e = exp(mu + sigma * (modes[e] . theta))
+// (lognormal) or mu + sigma * (modes[e] . theta), in FP64, into the slot's FP32 lane.
+// status: NONFINITE for a non-finite c_e, NOT_SPD for c_e <= 0 (first error kept).
+__global__ void k_field_coef(const double* __restrict__ modes, const double* __restrict__ theta, int m, double mu,
+                             double sigma, int lognormal, float* __restrict__ coef32, int n_el, int Bp, int slot,
+                             int* __restrict__ status) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += gridDim.x * blockDim.x) {
+        double g = 0.0;
+        for (int j = 0; j < m; ++j) g = fma(modes[(long long)e * m + j], theta[j], g);
+        const double v = lognormal ? exp(mu + sigma * g) : mu + sigma * g;
+        if (!isfinite(v)) atomicCAS(status, (int)POD2G_OK, (int)POD2G_NONFINITE);
+        else if (!(v > 0.0)) atomicCAS(status, (int)POD2G_OK, (int)POD2G_NOT_SPD);
+        coef32[(long long)e * Bp + slot] = __double2float_rn(v);
+    }
+}
+
 // The FP32 values of one slot's element operator, contiguous [nnzb][bs*bs]
 // (one thread per block row), from the same block-value routine the solver's
 // row kernels use.
@@ -247,6 +263,8 @@ static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
 
 // Element contexts: coefficients (FP64, device) -> the slot's FP32 lane, the FP32
 // operator values of that slot, then the common set-up.
+static int setup_elem_tail(pod2g_ctx* c, int slot, int* st);
+
 int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev) {
     const int T = POD2G_THREADS;
     P2G_CUDA(cudaMemsetAsync(c->d_setup_status + slot, 0, sizeof(int), c->stream));
@@ -254,6 +272,24 @@ int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev) {
     k_coef_convert<<<std::min(ceil_div(c->n_el, T), 8 * c->num_sms), T, 0, c->stream>>>(
         coef_dev, c->d_coef32, c->n_el, c->Bp, slot, st);
     P2G_TRY(pod2g_check_launch(c));
+    return setup_elem_tail(c, slot, st);
+}
+
+// Element contexts with a registered field: c_e(theta) on the device, then the same set-up.
+int setup_theta(pod2g_ctx* c, int slot, const double* theta_dev) {
+    const int T = POD2G_THREADS;
+    P2G_CUDA(cudaMemsetAsync(c->d_setup_status + slot, 0, sizeof(int), c->stream));
+    int* st = c->d_setup_status + slot;
+    k_field_coef<<<std::min(ceil_div(c->n_el, T), 8 * c->num_sms), T, 0, c->stream>>>(
+        c->d_modes, theta_dev, c->field_m, c->field_mu, c->field_sigma, c->field_log, c->d_coef32, c->n_el, c->Bp,
+        slot, st);
+    P2G_TRY(pod2g_check_launch(c));
+    return setup_elem_tail(c, slot, st);
+}
+
+// FP32 operator values of the slot from its coefficients, then D^-1, K_c and its factor.
+static int setup_elem_tail(pod2g_ctx* c, int slot, int* st) {
+    const int T = POD2G_THREADS;
     const ElemOp E = elem_op(c);
     const int g = std::min(ceil_div(c->nb, T), 8 * c->num_sms);
     if (c->bs == 1) k_elem_stage<1><<<g, T, 0, c->stream>>>(E, c->d_row_ptr, c->nb, c->Bp, slot, c->d_stage32);
