@@ -608,12 +608,13 @@ int pod2g_set_theta(pod2g_t c, int slot, const double* theta) {
 int pod2g_set_values_batch_dev(pod2g_t c, int nslots, const int* slots, const double* values_dev, int* status) {
     if (!c || !slots || !values_dev || nslots < 1 || nslots > c->B) return POD2G_INVALID_ARG;
     if (c->serving || c->elem) return POD2G_INVALID_ARG;
-    const size_t tot = (size_t)c->nnzb * c->bs * c->bs;
+    std::vector<char> seen(c->B, 0);
     for (int i = 0; i < nslots; ++i) {
-        if (slots[i] < 0 || slots[i] >= c->B) return POD2G_INVALID_ARG;
+        if (slots[i] < 0 || slots[i] >= c->B || seen[slots[i]]) return POD2G_INVALID_ARG;
+        seen[slots[i]] = 1;
         c->setup_ok[slots[i]] = 0;
-        P2G_TRY(setup_values(c, slots[i], values_dev + i * tot));
     }
+    P2G_TRY(setup_values_batch(c, nslots, slots, values_dev));
     return finish_setup(c, nslots, slots, status);
 }
 

@@ -340,6 +340,7 @@ enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT
 int plain_solve(pod2g_ctx* c, int slot, const double* b_dev, const double* x0_dev, double tol, int maxit,
                 double* x_dev, int* iters, double* relres, int* status);
 int setup_values(pod2g_ctx* c, int slot, const double* vals_dev);
+int setup_values_batch(pod2g_ctx* c, int nslots, const int* slots, const double* values_dev);
 int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev);
 int setup_theta(pod2g_ctx* c, int slot, const double* theta_dev);
 // doubles describing one instance: matrix values, or element coefficients

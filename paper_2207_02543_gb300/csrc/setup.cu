@@ -13,15 +13,15 @@
 
 namespace {
 
-// values (FP64, one instance, [nnzb][bs*bs]) -> FP32 contiguous copy and the
-// slot's lane of the interleaved array [nnzb*bs*bs][Bp]
+// values (FP64, one instance, [nnzb][bs*bs]) -> FP32 contiguous copy and (vals32
+// not null) the slot's lane of the interleaved array [nnzb*bs*bs][Bp]
 __global__ void k_convert_values(const double* __restrict__ v64, float* __restrict__ v32_stage,
                                  float* __restrict__ vals32, long long total, int Bp, int slot) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         float v = __double2float_rn(v64[e]);
         v32_stage[e] = v;
-        vals32[e * Bp + slot] = v;
+        if (vals32) vals32[e * Bp + slot] = v;
     }
 }
 
@@ -41,6 +41,59 @@ __global__ void k_dinv(const V* __restrict__ vals, const int32_t* __restrict__ d
     }
     if (dinv64) dinv64[d] = 1.0 / a;
     if (dinv32) dinv32[(long long)d * Bp + slot] = (float)(1.0 / a);
+}
+
+// Several instances at once: FP64 values [nslots][tot] -> FP32 lanes slots[i] of the
+// interleaved array, through a 32 x 32 shared-memory tile so that both the reads
+// (along entries) and the writes (along slots) are coalesced.
+__global__ void k_interleave(const double* __restrict__ v64, long long tot, int nslots, const int* __restrict__ slots,
+                             int Bp, float* __restrict__ vals32) {
+    __shared__ float tile[32][33];
+    const long long e0 = (long long)blockIdx.x * 32;
+    const int s0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int i = s0 + k;
+        const long long e = e0 + threadIdx.x;
+        if (i < nslots && e < tot) tile[k][threadIdx.x] = __double2float_rn(v64[(long long)i * tot + e]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int i = s0 + threadIdx.x;
+        const long long e = e0 + k;
+        if (i < nslots && e < tot) vals32[e * Bp + slots[i]] = tile[threadIdx.x][k];
+    }
+}
+
+// W = K Phi, double-float, one thread per (unknown row, group of 8 modes): the row's
+// values are read once for the 8 modes; each output accumulates in the same order as
+// a thread per output would.
+__global__ void k_w_df8(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                        const float* __restrict__ v32, const float* __restrict__ phi, int nb, int bs, int kp,
+                        float2* __restrict__ W) {
+    const int groups = kp / 8;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)nb * bs * groups;
+    if (t >= total) return;
+    const int g = (int)(t % groups);
+    const long long d = t / groups;
+    const int i = (int)(d / bs), rr = (int)(d - (long long)i * bs);
+    float hi[8], lo[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) { hi[m] = 0.f; lo[m] = 0.f; }
+    for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
+        const int j = col_idx[blk];
+        const float* vb = v32 + (long long)blk * bs * bs + rr * bs;
+        for (int cc = 0; cc < bs; ++cc) {
+            const float v = vb[cc];
+            const float4* ph = reinterpret_cast<const float4*>(phi + ((long long)j * bs + cc) * kp + 8 * g);
+            const float4 f0 = __ldg(ph), f1 = __ldg(ph + 1);
+            const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+            for (int m = 0; m < 8; ++m) df_acc_fma(hi[m], lo[m], v, f[m], 0.f);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) W[d * kp + 8 * g + m] = df_norm(hi[m], lo[m]);
 }
 
 // W = K Phi, double-float, one thread per (unknown row, mode m).
@@ -249,9 +302,9 @@ static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
                                                         c->Bp, slot, st);
     P2G_TRY(pod2g_check_launch(c));
     if (c->k > 0) {
-        long long tw = (long long)n * c->kp;
-        k_w_df<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, stage32, c->d_phi32, c->nb, c->bs,
-                                                     c->kp, (float2*)c->d_W);
+        long long tw = (long long)n * (c->kp / 8);
+        k_w_df8<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, stage32, c->d_phi32, c->nb,
+                                                      c->bs, c->kp, (float2*)c->d_W);
         P2G_TRY(pod2g_check_launch(c));
         int ga = std::max(1, std::min(2 * c->num_sms, ceil_div(n, 256)));
         k_ac<true><<<ga, T, 0, c->stream>>>(c->d_phi32, c->d_W, n, c->k, c->kp, c->d_ac_part,
@@ -299,7 +352,28 @@ static int setup_elem_tail(pod2g_ctx* c, int slot, int* st) {
     return setup_from_stage32(c, slot, st);
 }
 
-int setup_values(pod2g_ctx* c, int slot, const double* vals_dev) {
+int setup_values(pod2g_ctx* c, int slot, const double* vals_dev, bool lane_done);
+
+// Set-up of several slots (values_dev: nslots consecutive instances): on the mixed
+// paths the interleaved lanes of all of them are written by one tiled kernel first.
+int setup_values_batch(pod2g_ctx* c, int nslots, const int* slots, const double* values_dev) {
+    const long long tot = (long long)c->nnzb * c->bs * c->bs;
+    const bool batch = c->precision != POD2G_FP64 && nslots > 1;
+    if (batch) {
+        int* d_slots = (int*)(c->d_mask + c->Bp);
+        P2G_CUDA(cudaMemcpyAsync(d_slots, slots, sizeof(int) * nslots, cudaMemcpyHostToDevice, c->stream));
+        dim3 grid((unsigned)((tot + 31) / 32), (unsigned)((nslots + 31) / 32)), block(32, 8);
+        k_interleave<<<grid, block, 0, c->stream>>>(values_dev, tot, nslots, d_slots, c->Bp, c->d_vals32);
+        P2G_TRY(pod2g_check_launch(c));
+    }
+    for (int i = 0; i < nslots; ++i) P2G_TRY(setup_values(c, slots[i], values_dev + (size_t)i * tot, batch));
+    return POD2G_OK;
+}
+
+int setup_values(pod2g_ctx* c, int slot, const double* vals_dev) { return setup_values(c, slot, vals_dev, false); }
+
+// lane_done: the slot's lane of the interleaved values was already written
+int setup_values(pod2g_ctx* c, int slot, const double* vals_dev, bool lane_done) {
     const long long total = (long long)c->nnzb * c->bs * c->bs;
     const int T = POD2G_THREADS;
     const int n = c->n;
@@ -326,7 +400,8 @@ int setup_values(pod2g_ctx* c, int slot, const double* vals_dev) {
         }
     } else {
         int g = std::min(ceil_div(total, T), 8 * c->num_sms);
-        k_convert_values<<<g, T, 0, c->stream>>>(vals_dev, c->d_stage32, c->d_vals32, total, c->Bp, slot);
+        k_convert_values<<<g, T, 0, c->stream>>>(vals_dev, c->d_stage32, lane_done ? nullptr : c->d_vals32, total,
+                                                 c->Bp, slot);
         P2G_TRY(pod2g_check_launch(c));
         P2G_TRY(setup_from_stage32(c, slot, st));
     }
