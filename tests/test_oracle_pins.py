@@ -436,3 +436,22 @@ def test_gauss_seidel_smoother_needs_fewer_pcg_iterations():
     assert sgs.iters < jac.iters
     xs = np.linalg.solve(K.toarray(), f)
     assert np.linalg.norm(sgs.x - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+# ----------------------------------------------------------------------------- Section 3.3 steps 3-4
+def test_rom_solution_is_the_galerkin_projection():
+    """x_rom = Phi u_r with K_r u_r = Phi^T f: residual orthogonal to span(Phi), the K-norm
+    best approximation of x* in span(Phi) (checked against a least-squares solve in the
+    K-inner product), exact when x* lies in span(Phi)."""
+    P, K = _small_system(30, ne=6)
+    Kd = K.toarray()
+    Phi = _basis(K, 5)
+    f = P.f0
+    x = O.rom_solution(K, Phi, f)
+    assert np.abs(Phi.T @ (f - Kd @ x)).max() < 1e-12 * np.abs(f).max()
+    xs = np.linalg.solve(Kd, f)
+    Lk = np.linalg.cholesky(Kd)                      # ||v||_K = ||L^T v||_2
+    coef, *_ = np.linalg.lstsq(Lk.T @ Phi, Lk.T @ xs, rcond=None)
+    assert np.allclose(x, Phi @ coef, rtol=1e-9, atol=1e-12 * np.abs(xs).max())
+    c = np.random.default_rng(3).standard_normal(5)
+    assert np.allclose(O.rom_solution(K, Phi, Kd @ (Phi @ c)), Phi @ c, rtol=1e-10, atol=1e-12)
