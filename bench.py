@@ -412,8 +412,12 @@ def gb300_arm(args):
                                    "iters": its, "ratio_batched_over_plain": value / (1.0 / statistics.mean(times))}
         # serving: Poisson arrivals at ~70% of the batched throughput, continuous batching
         if not args.no_serve:
-            extra["serving"] = serve_latency(s, pkg, wl, vals_h, b_h, rate=0.7 * value, nreq=args.serve_requests,
-                                             tol=tol, maxit=maxit)
+            loads = [float(v) for v in args.serve_loads.split(",")]
+            runs = [dict(serve_latency(s, pkg, wl, vals_h, b_h, rate=f * value, nreq=args.serve_requests, tol=tol,
+                                       maxit=maxit), load=f) for f in loads]
+            extra["serving"] = runs[0]
+            if len(runs) > 1:
+                extra["serving_loads"] = runs
         # CPU baseline: the oracle on a bounded sample (single thread)
         if not args.no_cpu:
             try:
@@ -498,6 +502,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=128)
+    ap.add_argument("--serve-loads", default="0.7",
+                    help="Poisson arrival rates as fractions of the measured batch throughput, e.g. 0.5,0.7,0.9")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling of smaller cases)")
     ap.add_argument("--batch", type=int, default=0, help="instances per step (default: the workload's batch)")
     ap.add_argument("--method", default="pcg", choices=["pcg", "stationary"],
