@@ -37,3 +37,18 @@ def test_kernel_bytes_model():
 def test_measured_peak_fallback(tmp_path, monkeypatch):
     peaks, kind = bench.measured_peaks()
     assert kind in ("measured", "fallback") and peaks["hbm_gbs"] > 1000
+
+
+def test_oracle_timing_cli_reports_iterations():
+    """The CPU-baseline leg runs the oracle in a fresh single-threaded process and reads one JSON line."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    for method, smoother in (("pcg", "jacobi"), ("stationary", "sgs")):
+        r = subprocess.run([sys.executable, "-m", "oracle.timing", "q1_16", "0", "full", "1e-8", method, smoother],
+                           cwd=root, env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-500:]
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        assert out["status"] == 0 and out["relres"] <= 1e-8 and out["iterations"] > 0
+        assert out["seconds_per_iteration"] > 0
