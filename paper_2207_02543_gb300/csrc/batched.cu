@@ -155,51 +155,18 @@ __device__ __forceinline__ float2 df_of(float a) { return make_float2(a, 0.f); }
 // Prefetching loop over the blocks b0..b1 of one block row: for each group of
 // UNROLL blocks, `fetch(u, blk, j)` issues the loads of block blk (column j) into
 // slot u, then `use(u)` consumes them. Blocks past the row end are skipped.
-// With ROW_PIPE, the loads of the next group are issued before the current group
-// is consumed (two groups of U slots, alternating; the callers' per-slot arrays
-// then hold RB_SLOTS(U) = 2U entries).
-#ifndef ROW_PIPE
-#define ROW_PIPE 0
-#endif
-#define RB_SLOTS(U) (ROW_PIPE ? 2 * (U) : (U))
 template <int U = UNROLL, class Fetch, class Use>
 __device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, int b0, int b1, Fetch fetch, Use use) {
-    if (!ROW_PIPE) {
-        for (int blk0 = b0; blk0 < b1; blk0 += U) {
-            int jj[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) jj[u] = (blk0 + u < b1) ? __ldg(col_idx + blk0 + u) : -1;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (jj[u] >= 0) fetch(u, blk0 + u, jj[u]);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (jj[u] >= 0) use(u);
-        }
-        return;
-    }
-    int ja[U], jb[U];
-    auto issue = [&](int blk0, int* jj, int base) {
+    for (int blk0 = b0; blk0 < b1; blk0 += U) {
+        int jj[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) jj[u] = (blk0 + u < b1) ? __ldg(col_idx + blk0 + u) : -1;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (jj[u] >= 0) fetch(base + u, blk0 + u, jj[u]);
-    };
-    if (b0 >= b1) return;
-    issue(b0, ja, 0);
-    for (int blk0 = b0; blk0 < b1; blk0 += 2 * U) {
-        const bool second = blk0 + U < b1;
-        if (second) issue(blk0 + U, jb, U);
+            if (jj[u] >= 0) fetch(u, blk0 + u, jj[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (ja[u] >= 0) use(u);
-        if (second) {
-            if (blk0 + 2 * U < b1) issue(blk0 + 2 * U, ja, 0);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (jb[u] >= 0) use(U + u);
-        }
+            if (jj[u] >= 0) use(u);
     }
 }
 
@@ -300,9 +267,9 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
             float ah[BS], al[BS];
 #pragma unroll
             for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
-            float2 xj[RB_SLOTS(UNROLL_DF)][BS];
-            float v[RB_SLOTS(UNROLL_DF)][BS * BS];
-            uint64_t dsc[RB_SLOTS(UNROLL_DF)];
+            float2 xj[UNROLL_DF][BS];
+            float v[UNROLL_DF][BS * BS];
+            uint64_t dsc[UNROLL_DF];
             float ce[MF ? POD2G_ELEM_RE : 1];
             if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
@@ -391,9 +358,9 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
             float ah[BS], al[BS];
 #pragma unroll
             for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
-            float2 pj[RB_SLOTS(UNROLL_DF)][BS];
-            float v[RB_SLOTS(UNROLL_DF)][BS * BS];
-            uint64_t dsc[RB_SLOTS(UNROLL_DF)];
+            float2 pj[UNROLL_DF][BS];
+            float v[UNROLL_DF][BS * BS];
+            uint64_t dsc[UNROLL_DF];
             float ce[MF ? POD2G_ELEM_RE : 1];
             if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
@@ -487,8 +454,8 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
 #pragma unroll
             for (int a = 0; a < BS; ++a) acc[a] = 0.f;
             if (PRE) {
-                float yj[RB_SLOTS(UNROLL)][BS], v[RB_SLOTS(UNROLL)][BS * BS];
-                uint64_t dsc[RB_SLOTS(UNROLL)];
+                float yj[UNROLL][BS], v[UNROLL][BS * BS];
+                uint64_t dsc[UNROLL];
                 float ce[MF ? POD2G_ELEM_RE : 1];
                 if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
@@ -866,9 +833,9 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
         for (int a = 0; a < BS; ++a) acc[a] = 0.f;
 #pragma unroll
         for (int e = 0; e < BS * BS; ++e) vd[e] = 0.f;
-        float yj[RB_SLOTS(UNROLL)][BS], v[RB_SLOTS(UNROLL)][BS * BS];
-        int jj[RB_SLOTS(UNROLL)];
-        uint64_t dsc[RB_SLOTS(UNROLL)];
+        float yj[UNROLL][BS], v[UNROLL][BS * BS];
+        int jj[UNROLL];
+        uint64_t dsc[UNROLL];
         float ce[MF ? POD2G_ELEM_RE : 1];
         if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
         row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
@@ -933,8 +900,8 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
 #pragma unroll
             for (int a = 0; a < BS; ++a) acc[a] = 0.f;
             if (POST) {
-                float yj[RB_SLOTS(UNROLL)][BS], v[RB_SLOTS(UNROLL)][BS * BS];
-                uint64_t dsc[RB_SLOTS(UNROLL)];
+                float yj[UNROLL][BS], v[UNROLL][BS * BS];
+                uint64_t dsc[UNROLL];
                 float ce[MF ? POD2G_ELEM_RE : 1];
                 if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],

@@ -96,26 +96,6 @@ __global__ void k_w_df8(const int32_t* __restrict__ row_ptr, const int32_t* __re
     for (int m = 0; m < 8; ++m) W[d * kp + 8 * g + m] = df_norm(hi[m], lo[m]);
 }
 
-// W = K Phi, double-float, one thread per (unknown row, mode m).
-__global__ void k_w_df(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                       const float* __restrict__ v32, const float* __restrict__ phi, int nb, int bs, int kp,
-                       float2* __restrict__ W) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long total = (long long)nb * bs * kp;
-    if (t >= total) return;
-    int m = (int)(t % kp);
-    long long d = t / kp;
-    int i = (int)(d / bs), rr = (int)(d - (long long)i * bs);
-    float hi = 0.f, lo = 0.f;
-    for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
-        int j = col_idx[blk];
-        const float* vb = v32 + (long long)blk * bs * bs + rr * bs;
-        for (int cc = 0; cc < bs; ++cc)
-            df_acc_fma(hi, lo, vb[cc], phi[((long long)j * bs + cc) * kp + m], 0.f);
-    }
-    W[d * kp + m] = df_norm(hi, lo);
-}
-
 // W = K Phi in FP64.
 __global__ void k_w_f64(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                         const double* __restrict__ v64, const double* __restrict__ phi, int nb, int bs, int kp,
