@@ -44,10 +44,6 @@ int dev_alloc(pod2g_ctx* c, void** p, size_t bytes) {
     return POD2G_OK;
 }
 
-static double now_s() {
-    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
 // FP64 -> nearest BF16 (round to nearest even on the FP64 significand), as FP32.
 static float round_bf16(double v) {
     uint64_t u;

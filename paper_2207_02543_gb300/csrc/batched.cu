@@ -778,7 +778,8 @@ k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restric
        const float* __restrict__ phi, const float* __restrict__ ec, float* y, const SlotScalars* __restrict__ sc,
        long long n) {
     extern __shared__ float s_ec[];  // [Bp][KP + 1] (odd row stride: no bank conflicts across slots)
-    for (int e = threadIdx.x; e < D.Bp * KP; e += blockDim.x) s_ec[(e / KP) * (KP + 1) + e % KP] = ec[e];
+    if constexpr (KP > 0)
+        for (int e = threadIdx.x; e < D.Bp * KP; e += blockDim.x) s_ec[(e / KP) * (KP + 1) + e % KP] = ec[e];
     __syncthreads();
     const int lane = threadIdx.x & (D.Bp - 1);
     if (sc[lane].state != want) return;
@@ -1122,7 +1123,10 @@ static void launch_prol(pod2g_ctx* c, Dims D, int want) {
 template <int BS, int MF>
 static void launch_post(pod2g_ctx* c, Dims D, int want) {
     dim3 g(D.G), t(POD2G_THREADS);
-    if (c->smoother == POD2G_SMOOTHER_SGS)  // s is final: only r^T s and beta
+    // Gauss-Seidel: s is already final in place; k_post without its SpMV only forms r^T s and
+    // beta. Its y and s then name the same buffer: each element is read and written back with
+    // the same value by the same thread (beta_pr is 0, so s is not read), nothing else touches it.
+    if (c->smoother == POD2G_SMOOTHER_SGS)
         k_post<BS, 0, MF><<<g, t, 0, c->stream>>>(D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, elem_op(c),
                                                   c->d_dinv32, c->d_rdf, c->d_s32, c->d_s32, c->d_part,
                                                   c->d_counters + CNT_POST, c->d_sc);
