@@ -52,3 +52,21 @@ def test_oracle_timing_cli_reports_iterations():
         out = json.loads(r.stdout.strip().splitlines()[-1])
         assert out["status"] == 0 and out["relres"] <= 1e-8 and out["iterations"] > 0
         assert out["seconds_per_iteration"] > 0
+
+
+def test_reference_arm_line_matches_the_gpu_arm_contract():
+    """`bench.py --impl reference` times the oracle on the same workload and prints the GPU arm's
+    metric, with impl, cpu_baseline and e2e keys (small workload, CPU only)."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "q1_16", "--steps", "1",
+                        "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-800:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "solves/s at rel. residual 1e-8 (batched POD-2G-PCG)"
+    assert line["unit"] == "solves/s" and line["higher_is_better"] is True and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert "225 dofs" in line["config"]["workload"]
