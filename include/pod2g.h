@@ -101,14 +101,14 @@ typedef struct {
 /* Per-context options; fill with pod2g_default_opts and override. */
 typedef struct {
     double omega;             /* damped-Jacobi weight (default 2/3); needs omega * rho(D^-1 K) < 2 */
-    int pre;                  /* r1: pre-relaxation sweeps (default 1) */
-    int post;                 /* r2: post-relaxation sweeps (default 1) */
+    int pre;                  /* r1: pre-relaxation sweeps (default 1; 0..8 FP64, 0 or 1 mixed) */
+    int post;                 /* r2: post-relaxation sweeps (default 1; 0..8 FP64, 0 or 1 mixed) */
     int precision;            /* POD2G_FP64 / POD2G_MIXED_FP32PHI / POD2G_MIXED_BF16PHI */
     int beta_pr;              /* 0: beta = r_{k+1}^T s_{k+1} / r_k^T s_k (Algorithm 1); 1: Polak-Ribiere */
     int max_batch;            /* number of instance slots (1..256) */
     size_t hbm_budget;        /* bytes the context may allocate; 0 = no limit */
     int64_t spin_limit;       /* bound on host polling iterations of a solve (0 = default) */
-    int chunk;                /* PCG iterations per CUDA-graph launch in the batched path (even, default 8) */
+    int chunk;                /* PCG iterations per CUDA-graph launch in the batched path (default 8) */
     void* stream;             /* cudaStream_t to run on; NULL = a stream owned by the context */
     int method;               /* POD2G_PCG (default) or POD2G_STATIONARY; iters then counts cycles */
     int smoother;             /* POD2G_SMOOTHER_JACOBI (default) or POD2G_SMOOTHER_SGS. Nodes are
@@ -138,7 +138,8 @@ int pod2g_set_values(pod2g_t ctx, int slot, const double* values, int on_device)
 
 /* Same for several slots at once: values_dev points to nslots consecutive
  * instances (nslots * nnzb*bs*bs doubles, device memory). status[i] (host) gets
- * each slot's set-up status; the return value is the first non-OK status. */
+ * each slot's set-up status; the return value is the first non-OK status. A slot
+ * listed twice returns POD2G_INVALID_ARG. */
 int pod2g_set_values_batch_dev(pod2g_t ctx, int nslots, const int* slots,
                                const double* values_dev, int* status);
 
