@@ -50,14 +50,6 @@ import numpy as np
 OK, NOT_CONVERGED, BREAKDOWN, NOT_SPD = 0, 1, 2, 3
 
 
-def bsr_matrix(row_ptr, col_idx, values, bs):
-    """Scalar CSR matrix (scipy) from block-CSR arrays: values[nnzb, bs, bs] row-major blocks."""
-    import scipy.sparse as sp
-    values = np.asarray(values, dtype=np.float64).reshape(-1, bs, bs)
-    n = (len(row_ptr) - 1) * bs
-    return sp.bsr_matrix((values, np.asarray(col_idx), np.asarray(row_ptr)), shape=(n, n)).tocsr()
-
-
 def jacobi_inverse_diagonal(K) -> np.ndarray:
     """D^{-1} with D = diag(K) (the Jacobi preconditioner T = diag(K), Section 2.1)."""
     d = np.asarray(K.diagonal(), dtype=np.float64)

@@ -155,8 +155,11 @@ def _krylov_min(Kd, f, x0, Bd, k):
     return x0 + V @ y
 
 
+@pytest.mark.parametrize("beta", ["fr", "pr"])
 @pytest.mark.parametrize("precond", ["identity", "jacobi", "pod2g"])
-def test_pcg_iterates_minimise_energy_norm(precond):
+def test_pcg_iterates_minimise_energy_norm(precond, beta):
+    # With a fixed SPD preconditioner r_{k+1}^T s_k = 0, so the Polak-Ribiere beta equals the
+    # Algorithm 1 ratio and both give the K-norm minimiser over the preconditioned Krylov space.
     P, K = _small_system(8, ne=6)
     n = K.shape[0]
     Kd = K.toarray()
@@ -170,7 +173,7 @@ def test_pcg_iterates_minimise_energy_norm(precond):
     else:
         app = O.pod2g_preconditioner(K, O.pod2g_setup(K, _basis(K, 3), 2 / 3))
     Bd = np.column_stack([app(e) for e in np.eye(n)])
-    res = O.pcg(K, f, x0, app, 1e-30, 6, record=True)
+    res = O.pcg(K, f, x0, app, 1e-30, 6, beta=beta, record=True)
     xs = np.linalg.solve(Kd, f)
     for k in range(1, 7):
         xk = res.iterates[k]["x"]
@@ -313,6 +316,86 @@ def test_planted_beta_mistake_is_caught(monkeypatch):
     assert np.linalg.norm(x - xb) > 1e-6 * np.linalg.norm(xb)
     good = O.pcg(K, f, None, app, 1e-30, 3)
     assert np.linalg.norm(good.x - xb) <= 1e-9 * np.linalg.norm(xb)
+
+
+class _VaryingPreconditioner:
+    """s = B_j r for the j-th application: B_j = D^{-1} scaled by a seeded positive diagonal
+    that changes on every call (symmetric and positive definite, but not the same operator
+    twice), so that r_{k+1}^T s_k != 0 and the two beta forms differ."""
+
+    def __init__(self, K, seed):
+        self.dinv = 1.0 / K.diagonal()
+        self.rng = np.random.default_rng(seed)
+
+    def __call__(self, r):
+        return self.dinv * self.rng.uniform(0.5, 2.0, r.shape[0]) * r
+
+
+def test_polak_ribiere_conjugacy_defect_under_a_varying_preconditioner():
+    # For any preconditioner sequence, p_{k+1} = s_{k+1} + beta p_k with K p_k = (r_k - r_{k+1}) / alpha_k
+    # and alpha_k p_k^T K p_k = r_k^T s_k gives
+    #   alpha_k p_{k+1}^T K p_k = s_{k+1}^T r_k - s_{k+1}^T r_{k+1} + beta r_k^T s_k.
+    # The Polak-Ribiere beta r_{k+1}^T (s_{k+1} - s_k) / r_k^T s_k makes the right-hand side
+    # s_{k+1}^T r_k - r_{k+1}^T s_k (zero for a fixed symmetric preconditioner), the Algorithm 1
+    # ratio makes it s_{k+1}^T r_k. Both are checked on the recorded iterates, where the two
+    # forms give different directions.
+    P, K = _small_system(8, ne=6)
+    Kd = K.toarray()
+    f = np.random.default_rng(3).standard_normal(K.shape[0])
+    recs = {}
+    for beta in ("pr", "fr"):
+        res = O.pcg(K, f, None, _VaryingPreconditioner(K, 11), 1e-30, 6, beta=beta, record=True)
+        R = res.iterates
+        recs[beta] = R
+        for k in range(1, 5):
+            rk, sk, pk = R[k]["r"], R[k]["s"], R[k]["p"]
+            r1, s1, p1 = R[k + 1]["r"], R[k + 1]["s"], R[k + 1]["p"]
+            alpha = (rk @ sk) / (pk @ Kd @ pk)
+            lhs = alpha * (p1 @ Kd @ pk)
+            rhs = s1 @ rk - (r1 @ sk if beta == "pr" else 0.0)
+            scale = abs(s1 @ rk) + abs(r1 @ sk) + abs(s1 @ r1)
+            assert abs(lhs - rhs) <= 1e-9 * scale, (beta, k, lhs, rhs)
+    # the two forms really differ here (the pin above is not vacuous)
+    d = np.linalg.norm(recs["pr"][4]["x"] - recs["fr"][4]["x"])
+    assert d > 1e-6 * np.linalg.norm(recs["fr"][4]["x"])
+
+
+def test_planted_polak_ribiere_mistakes_are_caught():
+    # copies of the PR update with a wrong sign inside, or the new r^T s as denominator, break
+    # one of the two pins above (varying-preconditioner identity, or the fixed-preconditioner
+    # Krylov minimiser)
+    P, K = _small_system(8, ne=6)
+    n = K.shape[0]
+    Kd = K.toarray()
+    f = np.random.default_rng(2).standard_normal(n)
+
+    def run(app, rule, steps):
+        x, r = np.zeros(n), f.copy()
+        s = app(r); p = s.copy(); rs = r @ s
+        out = []
+        for _ in range(steps):
+            q = K @ p; a = rs / (p @ q); x = x + a * p; r_new = r - a * q
+            s_new = app(r_new); rs_new = r_new @ s_new
+            b = rule(r_new, s_new, s, rs, rs_new)
+            p_new = s_new + b * p
+            out.append((a, r, s, p, r_new, s_new, p_new))
+            r, s, p, rs = r_new, s_new, p_new, rs_new
+        return x, out
+
+    wrong_sign = lambda r1, s1, s0, rs, rs1: r1 @ (s1 + s0) / rs  # noqa: E731
+    wrong_den = lambda r1, s1, s0, rs, rs1: r1 @ (s1 - s0) / rs1  # noqa: E731
+    # wrong sign: the conjugacy identity of the varying-preconditioner pin fails
+    _, out = run(_VaryingPreconditioner(K, 11), wrong_sign, 4)
+    bad = 0
+    for a, rk, sk, pk, r1, s1, p1 in out[1:]:
+        lhs = a * (p1 @ Kd @ pk)
+        rhs = s1 @ rk - r1 @ sk
+        bad += abs(lhs - rhs) > 1e-6 * (abs(s1 @ rk) + abs(r1 @ sk) + abs(s1 @ r1))
+    assert bad > 0
+    # wrong denominator: the fixed-preconditioner iterates leave the Krylov minimiser
+    x, _ = run(O.jacobi_preconditioner(K), wrong_den, 3)
+    xb = _krylov_min(Kd, f, np.zeros(n), np.diag(1 / K.diagonal()), 3)
+    assert np.linalg.norm(x - xb) > 1e-6 * np.linalg.norm(xb)
 
 
 # ----------------------------------------------------------------------------- Algorithm 2 as a solver
