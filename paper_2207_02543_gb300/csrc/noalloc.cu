@@ -75,7 +75,6 @@ __global__ void k_phi_rows(const double* __restrict__ phi_cm, long long n, int k
 }
 
 std::mutex g_mu;                                // serialises calls within the process
-unsigned char* g_addr[NA_MAX_DEV] = {nullptr};  // device address of the scratch, per device
 pod2g_ctx g_ctx[NA_MAX_DEV];                    // host-side state, constructed at library load
 double g_scal_host[NA_MAX_DEV][16];             // host mirror of the per-solve scalars
 
@@ -101,19 +100,26 @@ extern "C" int pod2g_solve_noalloc(int32_t n_brows, int32_t bs, int32_t nnzb, co
     pod2g_opts o;
     if (opts) o = *opts; else pod2g_default_opts(&o);
     if (!(o.omega > 0.0) || o.pre < 0 || o.post < 0 || o.pre > 8 || o.post > 8) return POD2G_INVALID_ARG;
+    // only the damped-Jacobi PCG solve is offered here
+    if (o.method != POD2G_PCG || o.smoother != POD2G_SMOOTHER_JACOBI) return POD2G_INVALID_ARG;
 
     std::lock_guard<std::mutex> lock(g_mu);
     int dev = 0;
     P2G_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NA_MAX_DEV) return POD2G_INVALID_ARG;
-    if (!g_addr[dev]) {
-        // once per device, with that device current: the device address of the array
-        void* p = nullptr;
-        P2G_CUDA(cudaGetSymbolAddress(&p, g_pod2g_scratch));
-        g_addr[dev] = (unsigned char*)p;
-    }
-    unsigned char* S = g_addr[dev];
+    // The device address of the array in the current device's context, looked up on every
+    // call (a cheap host query), so that a context torn down and re-created since the last
+    // call is never written through a stale pointer.
+    void* addr = nullptr;
+    P2G_CUDA(cudaGetSymbolAddress(&addr, g_pod2g_scratch));
+    unsigned char* S = (unsigned char*)addr;
     pod2g_ctx* c = &g_ctx[dev];
+    // On every return path, including errors, the caller's stream is drained before the lock
+    // is released, so that the next call never overwrites scratch that queued work still uses.
+    struct DrainOnExit {
+        cudaStream_t s;
+        ~DrainOnExit() { cudaStreamSynchronize(s); }
+    } drain{(cudaStream_t)stream};
     c->device = dev;
     c->nb = n_brows; c->bs = bs; c->n = (int)n; c->nnzb = nnzb; c->k = k; c->kp = pick_kp_small(k);
     c->precision = POD2G_FP64; c->pre = o.pre; c->post = o.post; c->beta_pr = o.beta_pr ? 1 : 0;

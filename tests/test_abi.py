@@ -65,3 +65,18 @@ def test_opts_struct_layout_matches(lib):
     assert all(b == 0xAB for b in bytes(buf)[size:])
     o = ctypes.cast(buf, ctypes.POINTER(pkg.Opts)).contents
     assert o.method == pkg.PCG and o.smoother == pkg.SMOOTHER_JACOBI and o.precision == pkg.MIXED_FP32PHI
+
+
+def test_noalloc_rejects_options_it_does_not_offer(lib):
+    """pod2g_solve_noalloc runs the damped-Jacobi PCG solve only: a Gauss-Seidel or stationary
+    request is refused with INVALID_ARG during argument validation, before any device work."""
+    import paper_2207_02543_gb300 as pkg
+    fake = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    it, rr, st = ctypes.c_int(0), ctypes.c_double(0.0), ctypes.c_int(0)
+    for field, value in (("smoother", pkg.SMOOTHER_SGS), ("method", pkg.STATIONARY)):
+        o = pkg.Opts()
+        lib.pod2g_default_opts(ctypes.byref(o))
+        setattr(o, field, value)
+        rc = lib.pod2g_solve_noalloc(4, 1, 4, fake, fake, fake, fake, 1, ctypes.byref(o), fake, None, 1e-8, 10,
+                                     fake, ctypes.byref(it), ctypes.byref(rr), ctypes.byref(st), None)
+        assert rc == pkg.INVALID_ARG, field
