@@ -26,7 +26,10 @@
  *   - Stopping rule: ||r_k||_2 <= tol * ||b||_2 on the recurrence residual,
  *     tested before every iteration (k = 0 included). iters = number of alpha
  *     updates. final relative residual = ||b - K x||_2 / ||b||_2 recomputed at
- *     exit. b = 0 gives x = 0, iters = 0, relres = 0.
+ *     exit in FP64 on every path: the stored matrix values (FP32-rounded on the
+ *     mixed paths, exact in FP64) times the returned x, accumulated with FP64
+ *     fused multiply-adds against the caller's FP64 b, FP64 sums of squares.
+ *     b = 0 gives x = 0, iters = 0, relres = 0.
  *   - Precision modes:
  *       POD2G_FP64          values, vectors, Phi and arithmetic in FP64; one
  *                           instance at a time, kernel by kernel, convergence
@@ -198,7 +201,9 @@ int pod2g_set_theta(pod2g_t ctx, int slot, const double* theta);
 int pod2g_set_theta_batch(pod2g_t ctx, int nslots, const int* slots, const double* theta, int* status);
 
 /* Solve one instance (Algorithm 3). b, x0 (NULL: zero) and x are host arrays of
- * n doubles. iters / relres may be NULL. */
+ * n doubles. iters / relres may be NULL. *relres is the true relative residual
+ * ||b - K x||_2 / ||b||_2 of the returned x, recomputed in FP64 at exit (see
+ * Conventions), not the recurrence residual of the stopping test. */
 int pod2g_solve(pod2g_t ctx, int slot, const double* b, const double* x0, double tol,
                 int maxit, double* x, int* iters, double* relres);
 
@@ -286,8 +291,9 @@ void pod2g_destroy(pod2g_t ctx);
  * [n_brows+1], col_idx_dev [nnzb], sorted columns, diagonal present), values_dev
  * (nnzb*bs*bs doubles, row-major blocks), phi_dev (n*k doubles, column-major, may
  * be NULL when k = 0), b_dev and x0_dev (n doubles; x0_dev NULL = zero). opts:
- * omega, pre, post, beta_pr are used (NULL = defaults); precision, max_batch,
- * hbm_budget, chunk, stream and method are ignored (the method is always PCG). Output: x_dev (n doubles, device);
+ * omega, pre, post, beta_pr are used (NULL = defaults); method must be POD2G_PCG and
+ * smoother POD2G_SMOOTHER_JACOBI (anything else returns POD2G_INVALID_ARG); precision,
+ * max_batch, hbm_budget, spin_limit, chunk and stream are ignored. Output: x_dev (n doubles, device);
  * iters, relres, status (host, may be NULL) as for pod2g_solve. stream: the
  * cudaStream_t to run on (NULL = the legacy default stream).
  *
@@ -295,14 +301,15 @@ void pod2g_destroy(pod2g_t ctx);
  * larger sizes return POD2G_TOO_LARGE before any device work. An invalid pattern
  * returns POD2G_INVALID_ARG.
  *
- * Set-up: the first call on a device (with that device current) looks up the
- * device address of the static array; make that first call before any CUDA stream
- * capture. Every call shares the array and overwrites what the previous call left
- * there; the counters that must start at zero are cleared at the start of each
+ * Set-up: every call looks up the device address of the static array in the current
+ * device's context (cudaGetSymbolAddress, a host query; the first such query on a
+ * device may initialise the module there, so make the first call before any CUDA
+ * stream capture). Every call shares the array and overwrites what the previous call
+ * left there; the counters that must start at zero are cleared at the start of each
  * call. Calls that overlap on the GPU would race on the array: the library
- * serialises calls made from one process with a lock, and each call returns only
- * after its GPU work has finished. Returns the solve status (POD2G_OK when
- * converged), or an error code. */
+ * serialises calls made from one process with a lock, and each call, on every return
+ * path including errors, waits for the work it queued on `stream` before it returns.
+ * Returns the solve status (POD2G_OK when converged), or an error code. */
 #define POD2G_NOALLOC_MAX_N 16384
 #define POD2G_NOALLOC_MAX_K 32
 int pod2g_solve_noalloc(int32_t n_brows, int32_t bs, int32_t nnzb, const int32_t* row_ptr_dev,

@@ -104,7 +104,7 @@ static void free_all(pod2g_ctx* c) {
                     c->d_setup_status, c->d_stage, c->d_stage32, c->d_W, c->d_ac_part, c->d_Ac, c->d_counters,
                     c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
                     c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
-                    c->d_pdf, c->d_qdf, c->d_bdf, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
+                    c->d_pdf, c->d_qdf, c->d_bdf, c->d_b64, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
                     c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32, c->d_cnodes, c->d_colour, c->d_modes, c->d_theta};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -349,6 +349,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
         ALLOC(c->d_pdf, sizeof(float2) * n * Bp);
         ALLOC(c->d_qdf, sizeof(float2) * n * Bp);
         ALLOC(c->d_bdf, sizeof(float2) * n * Bp);
+        ALLOC(c->d_b64, sizeof(double) * n * Bp);
         ALLOC(c->d_s32, sizeof(float) * n * Bp);
         ALLOC(c->d_y32, sizeof(float) * n * Bp);
         ALLOC(c->d_ec, sizeof(float) * std::max(1, Bp * kp));
@@ -418,6 +419,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
              cudaMemset(c->d_pdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_qdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_bdf, 0, sizeof(float2) * n * Bp) == cudaSuccess &&
+             cudaMemset(c->d_b64, 0, sizeof(double) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_s32, 0, sizeof(float) * n * Bp) == cudaSuccess &&
              cudaMemset(c->d_y32, 0, sizeof(float) * n * Bp) == cudaSuccess;
     }

@@ -59,6 +59,17 @@ namespace cg = cooperative_groups;
 #ifndef ROW_MINB_DF
 #define ROW_MINB_DF 5
 #endif
+// 3 x 3 blocks keep twice the operands of a 2 x 2 block in flight: their row kernels
+// request fewer resident CTAs (64 registers) so that nothing spills
+#ifndef ROW_MINB_BS3
+#define ROW_MINB_BS3 4
+#endif
+#define MINB(BS, M) ((BS) == 3 ? ROW_MINB_BS3 : (M))
+// L2 bulk prefetch of the row stream `ROW_PF` grid-stride passes ahead (0: off; measured
+// slower than no prefetch on the 2D elasticity workload at distance 1)
+#ifndef ROW_PF
+#define ROW_PF 0
+#endif
 
 namespace {
 
@@ -153,17 +164,24 @@ __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a
 __device__ __forceinline__ float2 df_of(float a) { return make_float2(a, 0.f); }
 
 // Prefetching loop over the blocks b0..b1 of one block row: for each group of
-// UNROLL blocks, `fetch(u, blk, j)` issues the loads of block blk (column j) into
-// slot u, then `use(u)` consumes them. Blocks past the row end are skipped.
-template <int U = UNROLL, class Fetch, class Use>
-__device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, int b0, int b1, Fetch fetch, Use use) {
+// UNROLL blocks, `fetch_blk(u, blk)` issues the loads that depend only on the block
+// index (per-slot values, element descriptors) together with the column indices, then
+// `fetch_vec(u, j)` the gathers of vector entries at column j, then `use(u)` consumes
+// slot u. The value stream (the bulk of the bytes) thus never waits for a column index.
+// Blocks past the row end are skipped.
+template <int U = UNROLL, class FetchBlk, class FetchVec, class Use>
+__device__ __forceinline__ void row_blocks(const int32_t* __restrict__ col_idx, int b0, int b1, FetchBlk fetch_blk,
+                                           FetchVec fetch_vec, Use use) {
     for (int blk0 = b0; blk0 < b1; blk0 += U) {
         int jj[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) jj[u] = (blk0 + u < b1) ? __ldg(col_idx + blk0 + u) : -1;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (jj[u] >= 0) fetch(u, blk0 + u, jj[u]);
+            if (blk0 + u < b1) fetch_blk(u, blk0 + u);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (jj[u] >= 0) fetch_vec(u, jj[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (jj[u] >= 0) use(u);
@@ -213,11 +231,46 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
 }
 #define MBAR_POLLS (1u << 22)  // bound on the polls of one wait (each poll may suspend briefly)
 
+// ---------------------------------------------------------------------------- L2 prefetch of row streams
+// Bytes [b0, b1) of a device allocation (rounded out to 16 bytes; allocations are
+// 256-byte aligned and sized in multiples of 256, so the rounded range stays inside)
+// are requested into L2 by the bulk-copy engine: fire and forget, nothing waits on it.
+__device__ __forceinline__ void l2_prefetch_range(const void* base, long long b0, long long b1) {
+    b0 &= ~15LL;
+    b1 = (b1 + 15) & ~15LL;
+    const char* p = static_cast<const char*>(base);
+    for (long long o = b0; o < b1; o += 32768) {
+        const unsigned sz = (unsigned)min(32768LL, b1 - o);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(sz) : "memory");
+    }
+}
+
+// Row kernels walk items it = (block row << lgBp) + slot lane in grid-stride passes, so a
+// warp's 32 items are consecutive and cover one or more whole block rows (Bp <= 32) or
+// part of one (Bp > 32). The block data of those rows (column indices, and per-slot
+// values `bpb` bytes per block, or element descriptors) is one contiguous range. Lane 0
+// of the first warp of a row group prefetches into L2 the range the warp will read `ahead`
+// passes later (ahead = 0: the current pass), so that its dependent loads hit L2.
+__device__ __forceinline__ void prefetch_rows(const Dims& D, long long it, int ahead,
+                                              const int32_t* __restrict__ row_ptr, const int32_t* col_idx,
+                                              const void* bdata, long long bpb) {
+    const long long wbase = it - (threadIdx.x & 31);
+    if ((threadIdx.x & 31) != 0 || (wbase & (D.Bp - 1)) != 0) return;
+    const long long nxt = wbase + (long long)ahead * gridDim.x * blockDim.x;
+    const long long i_lo = nxt >> D.lgBp;
+    if (i_lo >= D.nb) return;
+    const long long i_hi = min((long long)D.nb - 1, (nxt + 31) >> D.lgBp);
+    const long long k0 = __ldg(row_ptr + i_lo), k1 = __ldg(row_ptr + i_hi + 1);
+    l2_prefetch_range(col_idx, 4 * k0, 4 * k1);
+    if (bdata) l2_prefetch_range(bdata, bpb * k0, bpb * k1);
+}
+
 // ---------------------------------------------------------------------------- load / store / residual
 // Joining lanes: b -> bdf, x0 -> xdf (zero if absent), p = q = 0.
 __global__ void k_load(const double* __restrict__ b, const double* __restrict__ x0, const int* __restrict__ slots,
-                       int nslots, int n, int Bp, float2* __restrict__ bdf, float2* __restrict__ xdf,
-                       float2* __restrict__ pdf, float2* __restrict__ qdf, float* __restrict__ s32) {
+                       int nslots, int n, int Bp, float2* __restrict__ bdf, double* __restrict__ b64,
+                       float2* __restrict__ xdf, float2* __restrict__ pdf, float2* __restrict__ qdf,
+                       float* __restrict__ s32) {
     long long total = (long long)nslots * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -225,6 +278,7 @@ __global__ void k_load(const double* __restrict__ b, const double* __restrict__ 
         long long d = e - (long long)r * n;
         long long o = d * Bp + slots[r];
         bdf[o] = df_from_double(b[e]);
+        b64[o] = b[e];
         xdf[o] = x0 ? df_from_double(x0[e]) : make_float2(0.f, 0.f);
         pdf[o] = make_float2(0.f, 0.f);
         qdf[o] = make_float2(0.f, 0.f);
@@ -245,12 +299,11 @@ __global__ void k_store(double* __restrict__ x, const int* __restrict__ slots, i
     }
 }
 
-// r = b - K x in double-float for masked lanes. init: writes r, sums ||b||^2 and
-// sets tol2 = tol^2 ||b||^2 (b = 0 or non-finite -> DONE). final: sums
-// ||b - K x||^2 into relres.
+// r = b - K x in double-float for masked lanes: writes r, sums ||b||^2 and sets
+// tol2 = tol^2 ||b||^2 (b = 0 or non-finite -> DONE).
 template <int BS, int MF>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB_DF)
-k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __restrict__ row_ptr,
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, MINB(BS, ROW_MINB_DF))
+k_resid(Dims D, const int* __restrict__ mask, const int32_t* __restrict__ row_ptr,
         const int32_t* __restrict__ col_idx, const float* __restrict__ vals, ElemOp E, const float2* __restrict__ x,
         const float2* __restrict__ b, float2* __restrict__ r, double* part, unsigned* counter, SlotScalars* sc) {
     __shared__ double s_tmp[POD2G_THREADS];
@@ -259,10 +312,19 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = mask[lane] != 0;
     float bh = 0.f, bl = 0.f, rh = 0.f, rl = 0.f;
-    if (on) {
-        const long long items = (long long)D.nb << D.lgBp;
-        for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
-             it += (long long)gridDim.x * blockDim.x) {
+    const long long items = (long long)D.nb << D.lgBp;
+    const bool warp_on = __any_sync(0xffffffffu, on);
+    const void* bdata = MF ? (const void*)E.desc : (const void*)vals;  // per-block data streamed with the rows
+    const long long bpb = MF ? 8LL : (long long)BS * BS * D.Bp * 4;
+    bool first = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        if (ROW_PF > 0 && warp_on) {
+            if (first) prefetch_rows(D, it, 0, row_ptr, col_idx, bdata, bpb);
+            prefetch_rows(D, it, ROW_PF, row_ptr, col_idx, bdata, bpb);
+            first = false;
+        }
+        if (on) {
             const int i = (int)(it >> D.lgBp);
             float ah[BS], al[BS];
 #pragma unroll
@@ -273,9 +335,7 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
             float ce[MF ? POD2G_ELEM_RE : 1];
             if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
-                [&](int u, int blk, int j) {
-#pragma unroll
-                    for (int cc = 0; cc < BS; ++cc) xj[u][cc] = x[((long long)j * BS + cc) * D.Bp + lane];
+                [&](int u, int blk) {
                     if constexpr (MF) {
                         dsc[u] = __ldg(E.desc + blk);
                     } else {
@@ -283,6 +343,10 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
 #pragma unroll
                         for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                     }
+                },
+                [&](int u, int j) {
+#pragma unroll
+                    for (int cc = 0; cc < BS; ++cc) xj[u][cc] = x[((long long)j * BS + cc) * D.Bp + lane];
                 },
                 [&](int u) {
                     if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
@@ -297,7 +361,7 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
                 const long long o = ((long long)i * BS + a) * D.Bp + lane;
                 float2 bv = b[o];
                 float2 rv = df_add(bv, df_neg(df_norm(ah[a], al[a])));
-                if (!final_mode) r[o] = rv;
+                r[o] = rv;
                 df_acc_fma(bh, bl, bv.x, bv.x, 2.f * bv.y);
                 df_acc_fma(rh, rl, rv.x, rv.x, 2.f * rv.y);
             }
@@ -311,18 +375,79 @@ k_resid(Dims D, int final_mode, const int* __restrict__ mask, const int32_t* __r
     double rr = grid_lane_total(part + D.Bp, D.NP, 2 * D.Bp, D.Bp, s_tmp);
     if ((int)threadIdx.x < D.Bp && mask[threadIdx.x]) {
         SlotScalars& s = sc[threadIdx.x];
-        if (final_mode) {
-            s.relres = s.bb > 0.0 ? sqrt(rr / s.bb) : 0.0;
-        } else {
-            s.bb = bb;
-            s.tol2 = s.tol2 * bb;  // host stored tol^2
-            if (bb == 0.0) {
-                s.state = SLOT_DONE; s.result = POD2G_OK; s.iters = 0;
-            } else if (!isfinite(bb) || !isfinite(rr)) {
-                s.state = SLOT_DONE; s.result = POD2G_NONFINITE;
+        s.bb = bb;
+        s.tol2 = s.tol2 * bb;  // host stored tol^2
+        if (bb == 0.0) {
+            s.state = SLOT_DONE; s.result = POD2G_OK; s.iters = 0;
+        } else if (!isfinite(bb) || !isfinite(rr)) {
+            s.state = SLOT_DONE; s.result = POD2G_NONFINITE;
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// The reported final residual ||b - K x||_2 / ||b||_2 in FP64 for masked lanes: the
+// stored FP32 values (exact in FP64) times x (the double-float iterate, hi + lo exact
+// in FP64) accumulated with FP64 fused multiply-adds, b the caller's FP64 right-hand
+// side, and FP64 sums of squares reduced in a fixed order.
+template <int BS, int MF>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_resid64(Dims D, const int* __restrict__ mask, const int32_t* __restrict__ row_ptr,
+          const int32_t* __restrict__ col_idx, const float* __restrict__ vals, ElemOp E, const float2* __restrict__ x,
+          const double* __restrict__ b64, double* part, unsigned* counter, SlotScalars* sc) {
+    __shared__ double s_tmp[POD2G_THREADS];
+    __shared__ double s_out[2 * POD2G_MAX_BP];
+    ELEM_SMEM_KREF(MF, E);
+    const int lane = threadIdx.x & (D.Bp - 1);
+    const bool on = mask[lane] != 0;
+    double bb = 0.0, rr = 0.0;
+    if (on) {
+        const long long items = (long long)D.nb << D.lgBp;
+        for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+             it += (long long)gridDim.x * blockDim.x) {
+            const int i = (int)(it >> D.lgBp);
+            double acc[BS];
+#pragma unroll
+            for (int a = 0; a < BS; ++a) acc[a] = 0.0;
+            float ce[MF ? POD2G_ELEM_RE : 1];
+            if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
+            for (int blk = row_ptr[i]; blk < row_ptr[i + 1]; ++blk) {
+                const int j = __ldg(col_idx + blk);
+                float v[BS * BS];
+                if constexpr (MF) {
+                    elem_block_values<BS>(__ldg(E.desc + blk), ce, s_kref, v);
+                } else {
+                    const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
+#pragma unroll
+                    for (int e = 0; e < BS * BS; ++e) v[e] = vb[e * D.Bp];
+                }
+                double xj[BS];
+#pragma unroll
+                for (int cc = 0; cc < BS; ++cc) {
+                    const float2 t = x[((long long)j * BS + cc) * D.Bp + lane];
+                    xj[cc] = (double)t.x + (double)t.y;
+                }
+#pragma unroll
+                for (int a = 0; a < BS; ++a)
+#pragma unroll
+                    for (int cc = 0; cc < BS; ++cc) acc[a] = fma((double)v[a * BS + cc], xj[cc], acc[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < BS; ++a) {
+                const double bv = b64[((long long)i * BS + a) * D.Bp + lane];
+                const double rv = bv - acc[a];
+                bb = fma(bv, bv, bb);
+                rr = fma(rv, rv, rr);
             }
         }
     }
+    cta_lane_sum(bb, D.Bp, s_tmp, s_out);
+    cta_lane_sum(rr, D.Bp, s_tmp, s_out + D.Bp);
+    cluster_store(s_out, 2 * D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
+    if (!last_cluster_arrive(counter, D.NP)) return;
+    const double btot = grid_lane_total(part, D.NP, 2 * D.Bp, D.Bp, s_tmp);
+    const double rtot = grid_lane_total(part + D.Bp, D.NP, 2 * D.Bp, D.Bp, s_tmp);
+    if ((int)threadIdx.x < D.Bp && mask[threadIdx.x]) sc[threadIdx.x].relres = btot > 0.0 ? sqrt(rtot / btot) : 0.0;
     if (threadIdx.x == 0) *counter = 0u;
 }
 
@@ -340,7 +465,7 @@ __global__ void k_p(Dims D, int want, const float* __restrict__ s, float2* __res
 
 // q = K p (double-float), partial p^T q; last cluster: alpha per slot.
 template <int BS, int MF>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB_DF)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, MINB(BS, ROW_MINB_DF))
 k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
        const float* __restrict__ vals, ElemOp E, const float2* __restrict__ p, float2* __restrict__ q, double* part,
        unsigned* counter, SlotScalars* sc) {
@@ -350,10 +475,19 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
     const int lane = threadIdx.x & (D.Bp - 1);
     const bool on = sc[lane].state == want;
     float dh = 0.f, dl = 0.f;
-    if (on) {
-        const long long items = (long long)D.nb << D.lgBp;
-        for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
-             it += (long long)gridDim.x * blockDim.x) {
+    const long long items = (long long)D.nb << D.lgBp;
+    const bool warp_on = __any_sync(0xffffffffu, on);
+    const void* bdata = MF ? (const void*)E.desc : (const void*)vals;  // per-block data streamed with the rows
+    const long long bpb = MF ? 8LL : (long long)BS * BS * D.Bp * 4;
+    bool first = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        if (ROW_PF > 0 && warp_on) {
+            if (first) prefetch_rows(D, it, 0, row_ptr, col_idx, bdata, bpb);
+            prefetch_rows(D, it, ROW_PF, row_ptr, col_idx, bdata, bpb);
+            first = false;
+        }
+        if (on) {
             const int i = (int)(it >> D.lgBp);
             float ah[BS], al[BS];
 #pragma unroll
@@ -364,9 +498,7 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
             float ce[MF ? POD2G_ELEM_RE : 1];
             if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
             row_blocks<UNROLL_DF>(col_idx, row_ptr[i], row_ptr[i + 1],
-                [&](int u, int blk, int j) {
-#pragma unroll
-                    for (int cc = 0; cc < BS; ++cc) pj[u][cc] = p[((long long)j * BS + cc) * D.Bp + lane];
+                [&](int u, int blk) {
                     if constexpr (MF) {
                         dsc[u] = __ldg(E.desc + blk);
                     } else {
@@ -374,6 +506,10 @@ k_spmv(Dims D, int want, const int32_t* __restrict__ row_ptr, const int32_t* __r
 #pragma unroll
                         for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                     }
+                },
+                [&](int u, int j) {
+#pragma unroll
+                    for (int cc = 0; cc < BS; ++cc) pj[u][cc] = p[((long long)j * BS + cc) * D.Bp + lane];
                 },
                 [&](int u) {
                     if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
@@ -434,7 +570,7 @@ __global__ void k_upd(Dims D, int want, float2* __restrict__ x, float2* __restri
 // 0 (PRE = 0) or a stored y1 (PRE = 2, Gauss-Seidel), r1 = r - K y1, written to
 // out (FP32); cluster partial sums of ||r||^2 go to part[cluster][slot].
 template <int BS, int MF>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, MINB(BS, ROW_MINB))
 k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
           const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
           const float* __restrict__ y1, float* __restrict__ out, double* part, const SlotScalars* __restrict__ sc) {
@@ -445,10 +581,19 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
     const bool on = sc[lane].state == want;
     float rr = 0.f;
     const float w = (float)D.omega;
-    if (on) {
-        const long long items = (long long)D.nb << D.lgBp;
-        for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
-             it += (long long)gridDim.x * blockDim.x) {
+    const long long items = (long long)D.nb << D.lgBp;
+    const bool warp_on = __any_sync(0xffffffffu, on);
+    const void* bdata = MF ? (const void*)E.desc : (const void*)vals;  // per-block data streamed with the rows
+    const long long bpb = MF ? 8LL : (long long)BS * BS * D.Bp * 4;
+    bool first = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        if (ROW_PF > 0 && warp_on) {
+            if (PRE && first) prefetch_rows(D, it, 0, row_ptr, col_idx, bdata, bpb);
+            if (PRE) prefetch_rows(D, it, ROW_PF, row_ptr, col_idx, bdata, bpb);
+            first = false;
+        }
+        if (on) {
             const int i = (int)(it >> D.lgBp);
             float acc[BS];
 #pragma unroll
@@ -459,18 +604,20 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
                 float ce[MF ? POD2G_ELEM_RE : 1];
                 if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
-                    [&](int u, int blk, int j) {
-#pragma unroll
-                        for (int cc = 0; cc < BS; ++cc) {
-                            const long long o = ((long long)j * BS + cc) * D.Bp + lane;
-                            yj[u][cc] = PRE == 2 ? y1[o] : w * dinv[o] * r[o].x;
-                        }
+                    [&](int u, int blk) {
                         if constexpr (MF) {
                             dsc[u] = __ldg(E.desc + blk);
                         } else {
                             const float* vb = vals + (long long)blk * BS * BS * D.Bp + lane;
 #pragma unroll
                             for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
+                        }
+                    },
+                    [&](int u, int j) {
+#pragma unroll
+                        for (int cc = 0; cc < BS; ++cc) {
+                            const long long o = ((long long)j * BS + cc) * D.Bp + lane;
+                            yj[u][cc] = PRE == 2 ? y1[o] : w * dinv[o] * r[o].x;
                         }
                     },
                     [&](int u) {
@@ -817,7 +964,7 @@ k_prol(Dims D, int want, const float* __restrict__ dinv, const float2* __restric
 // FROM0: the forward sweep from y = 0, where nodes of this and later colours
 // still read as 0 (their memory is not read).
 template <int BS, int MF, int BWD>
-__global__ void __launch_bounds__(POD2G_THREADS, ROW_MINB)
+__global__ void __launch_bounds__(POD2G_THREADS, MINB(BS, ROW_MINB))
 k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes, int cnt,
      const uint8_t* __restrict__ col_of, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
      const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
@@ -840,11 +987,7 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
         float ce[MF ? POD2G_ELEM_RE : 1];
         if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
         row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
-            [&](int u, int blk, int j) {
-                jj[u] = j;
-                const bool zero = from0 && (j == i || (int)col_of[j] >= colour);
-#pragma unroll
-                for (int cc = 0; cc < BS; ++cc) yj[u][cc] = zero ? 0.f : y[((long long)j * BS + cc) * D.Bp + lane];
+            [&](int u, int blk) {
                 if constexpr (MF) {
                     dsc[u] = __ldg(E.desc + blk);
                 } else {
@@ -852,6 +995,12 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
 #pragma unroll
                     for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                 }
+            },
+            [&](int u, int j) {
+                jj[u] = j;
+                const bool zero = from0 && (j == i || (int)col_of[j] >= colour);
+#pragma unroll
+                for (int cc = 0; cc < BS; ++cc) yj[u][cc] = zero ? 0.f : y[((long long)j * BS + cc) * D.Bp + lane];
             },
             [&](int u) {
                 if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
@@ -881,7 +1030,7 @@ k_gs(Dims D, int want, int from0, int colour, const int32_t* __restrict__ cnodes
 // s = y2 + omega D^-1 (r - K y2) (r2 = 1) or y2 (r2 = 0); partial r^T s (and
 // r^T s_old for Polak-Ribiere); last cluster: beta, JOINING -> ACTIVE.
 template <int BS, int POST, int MF>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, ROW_MINB)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, MINB(BS, ROW_MINB))
 k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
        const float* __restrict__ vals, ElemOp E, const float* __restrict__ dinv, const float2* __restrict__ r,
        const float* __restrict__ y, float* __restrict__ s, double* part, unsigned* counter, SlotScalars* sc) {
@@ -892,10 +1041,19 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
     const bool on = sc[lane].state == want;
     float h = 0.f, l = 0.f, xh = 0.f, xl = 0.f;
     const float w = (float)D.omega;
-    if (on) {
-        const long long items = (long long)D.nb << D.lgBp;
-        for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
-             it += (long long)gridDim.x * blockDim.x) {
+    const long long items = (long long)D.nb << D.lgBp;
+    const bool warp_on = __any_sync(0xffffffffu, on);
+    const void* bdata = MF ? (const void*)E.desc : (const void*)vals;  // per-block data streamed with the rows
+    const long long bpb = MF ? 8LL : (long long)BS * BS * D.Bp * 4;
+    bool first = true;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        if (ROW_PF > 0 && warp_on) {
+            if (POST && first) prefetch_rows(D, it, 0, row_ptr, col_idx, bdata, bpb);
+            if (POST) prefetch_rows(D, it, ROW_PF, row_ptr, col_idx, bdata, bpb);
+            first = false;
+        }
+        if (on) {
             const int i = (int)(it >> D.lgBp);
             float acc[BS];
 #pragma unroll
@@ -906,9 +1064,7 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
                 float ce[MF ? POD2G_ELEM_RE : 1];
                 if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
                 row_blocks(col_idx, row_ptr[i], row_ptr[i + 1],
-                    [&](int u, int blk, int j) {
-#pragma unroll
-                        for (int cc = 0; cc < BS; ++cc) yj[u][cc] = y[((long long)j * BS + cc) * D.Bp + lane];
+                    [&](int u, int blk) {
                         if constexpr (MF) {
                             dsc[u] = __ldg(E.desc + blk);
                         } else {
@@ -916,6 +1072,10 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
 #pragma unroll
                             for (int e = 0; e < BS * BS; ++e) v[u][e] = vb[e * D.Bp];
                         }
+                    },
+                    [&](int u, int j) {
+#pragma unroll
+                        for (int cc = 0; cc < BS; ++cc) yj[u][cc] = y[((long long)j * BS + cc) * D.Bp + lane];
                     },
                     [&](int u) {
                         if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
@@ -1256,10 +1416,10 @@ int batched_load(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev
     P2G_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyHostToDevice, c->stream));
     const long long tot = (long long)nslots * c->n;
     k_load<<<elementwise_grid(c, tot), POD2G_THREADS, 0, c->stream>>>(
-        b_dev, x0_dev, d_slots, nslots, c->n, c->Bp, c->d_bdf, c->d_xdf, c->d_pdf, c->d_qdf, c->d_s32);
+        b_dev, x0_dev, d_slots, nslots, c->n, c->Bp, c->d_bdf, c->d_b64, c->d_xdf, c->d_pdf, c->d_qdf, c->d_s32);
     P2G_TRY(pod2g_check_launch(c));
     const ElemOp E = elem_op(c);
-    LAUNCH_BS(k_resid, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, 0, c->d_mask, c->d_row_ptr, c->d_col_idx,
+    LAUNCH_BS(k_resid, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, c->d_mask, c->d_row_ptr, c->d_col_idx,
                                                               c->d_vals32, E, c->d_xdf, c->d_bdf, c->d_rdf, c->d_part,
                                                               c->d_counters + CNT_RESID, c->d_sc));
     P2G_TRY(pod2g_check_launch(c));
@@ -1380,7 +1540,7 @@ int batched_run(pod2g_ctx* c, const std::vector<int>& lanes) {
     }
 }
 
-// true residual for the finished lanes, x out, per-slot results
+// true FP64 residual for the finished lanes, x out, per-slot results
 int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, int* iters, double* relres,
                      int* status) {
     Dims D = dims_of(c);
@@ -1390,9 +1550,9 @@ int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, 
     P2G_CUDA(cudaMemcpyAsync(c->d_mask, mask.data(), sizeof(int) * c->Bp, cudaMemcpyHostToDevice, c->stream));
     P2G_CUDA(cudaMemcpyAsync(d_slots, slots, sizeof(int) * nslots, cudaMemcpyHostToDevice, c->stream));
     const ElemOp E = elem_op(c);
-    LAUNCH_BS(k_resid, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, 1, c->d_mask, c->d_row_ptr, c->d_col_idx,
-                                                              c->d_vals32, E, c->d_xdf, c->d_bdf, c->d_rdf, c->d_part,
-                                                              c->d_counters + CNT_RESID, c->d_sc));
+    LAUNCH_BS(k_resid64, <<<D.G, POD2G_THREADS, 0, c->stream>>>(D, c->d_mask, c->d_row_ptr, c->d_col_idx,
+                                                                c->d_vals32, E, c->d_xdf, c->d_b64, c->d_part,
+                                                                c->d_counters + CNT_RESID, c->d_sc));
     P2G_TRY(pod2g_check_launch(c));
     const long long tot = (long long)nslots * c->n;
     k_store<<<elementwise_grid(c, tot), POD2G_THREADS, 0, c->stream>>>(x_dev, d_slots, nslots, c->n, c->Bp, c->d_xdf,

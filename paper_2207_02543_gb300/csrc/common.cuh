@@ -119,6 +119,7 @@ struct pod2g_ctx {
     float2* d_pdf = nullptr;
     float2* d_qdf = nullptr;
     float2* d_bdf = nullptr;
+    double* d_b64 = nullptr;            // [n][Bp] the right-hand sides in FP64 (final residual)
     float* d_s32 = nullptr;             // [n][Bp]
     float* d_y32 = nullptr;             // [n][Bp]
     float* d_ec = nullptr;              // [Bp][kp] coarse corrections

@@ -53,6 +53,8 @@ SPECS = {
     # mid-size case of the 2D elasticity family (profiling: a few GB on the device)
     "q4_256": Spec("q4_256", 17, "q4", 256, 8, 20, 100, 64, 2.0 / 3.0, "f32", "mixed", cov=0.3),
     "hex8_32": Spec("hex8_32", 18, "hex8", 32, 12, 30, 100, 32, 0.5, "bf16", "mixed", cov=0.4),
+    # 2D diffusion at the lane count and basis size of the 1024^2 serving member (16 slots, k = 25)
+    "q1_128": Spec("q1_128", 19, "q1", 128, 16, 25, 60, 16, 2.0 / 3.0, "f32", "mixed", sigma=0.5),
 }
 
 

@@ -46,7 +46,8 @@ def _relerr(a, b):
 
 
 @pytest.mark.parametrize("name,precision,method", [("q1_32", 1, 0), ("q4_16", 1, 0), ("hex8_8", 2, 0),
-                                                   ("q4_64", 1, 0), ("q1_32", 1, 1)])
+                                                   ("q4_64", 1, 0), ("q1_32", 1, 1), ("hex8_16", 2, 0),
+                                                   ("hex8_16", 2, 1)])
 def test_element_path_matches_assembled_and_oracle(pkg, name, precision, method):
     wl = Workload(name)
     P, Phi = wl.problem, pod_basis(wl)

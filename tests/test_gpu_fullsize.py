@@ -4,9 +4,10 @@
 k = 20 from 200 snapshots, 64 instances solved together exactly as bench.py does
 (device-resident FP64 values through pod2g_set_values_batch_dev, launch shapes from
 pod2g_autotune, pod2g_solve_batch_dev, tol 1e-8). Checks:
-  * every instance: status OK, the library's final residual equals an independent
-    FP64 CPU residual ||b - K x|| / ||b|| of the returned x (K from the FP32-rounded
-    values the mixed path solves), and it is <= 1.05e-8;
+  * every instance: status OK, the library's final residual (computed in FP64 on the
+    device) equals an independent FP64 CPU residual ||b - K x|| / ||b|| of the returned x
+    (K from the FP32-rounded values the mixed path solves) within the FP64 rounding-error
+    bound of the two summation orders, and it is <= 1.05e-8;
   * a sampled instance against the FP64 oracle run on the same rounded values and
     rounded basis: relative 2-norm error of x <= 1e-6 and iteration counts within +-2.
 """
@@ -61,12 +62,16 @@ def _run_batch(pkg, name, sample):
         K = P.csr(v)
         bn = np.linalg.norm(bh[i])
         true_rel = np.linalg.norm(bh[i] - K @ X[i]) / bn
-        # rounding-error bound of a computed residual b - K x: each row's terms |K_ij x_j| and
-        # |b_i| carry a relative error of at most ~u, u = 2^-47 for double-float (2^-53 FP64)
+        # Both sides compute b - K x in FP64 from the same FP32 values and the same x, in
+        # different summation orders. A row of m terms computed in FP64 is within
+        # gamma_m (|K||x| + |b|)_i of the exact value (gamma_m = m u / (1 - m u), u = 2^-53),
+        # so the two relative residuals differ by at most 2 gamma_m ||(|K||x| + |b|)|| / ||b||.
+        m = int(np.max(np.diff(K.indptr))) + 1
+        u = 2.0 ** -53
         scale = np.linalg.norm(abs(K) @ np.abs(X[i]) + np.abs(bh[i])) / bn
-        bound = 32 * 2.0 ** -47 * scale
+        bound = 2 * (m * u / (1 - m * u)) * scale
         assert true_rel <= 1.05 * TOL + bound, (i, true_rel, bound)
-        assert abs(true_rel - rel[i]) <= bound + 1e-3 * true_rel, (i, true_rel, rel[i], bound)
+        assert abs(true_rel - rel[i]) <= bound, (i, true_rel, rel[i], bound)
     phi_used = round_phi(Phi, wl.spec.phi_dtype)
     for i in sample:
         K = P.csr(round_f32(vals[i].cpu().numpy()).reshape(-1, P.bs, P.bs))

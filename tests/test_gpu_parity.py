@@ -17,6 +17,7 @@ from oracle import pod2g_oracle as O  # noqa: E402
 from synth.problems import Workload  # noqa: E402
 from synth.rounding import round_f32, round_phi  # noqa: E402
 from synth.snapshots import pod_basis  # noqa: E402
+from fp64_residual import assert_relres_matches  # noqa: E402
 
 TOL = 1e-8
 
@@ -84,7 +85,35 @@ def test_mixed_batched_matches_oracle(pkg, name, precision):
         assert _relerr(X[i], ref.x) <= 1e-6, (i, _relerr(X[i], ref.x))
         assert abs(int(iters[i]) - ref.iters) <= 2, (i, iters[i], ref.iters)
         assert rel[i] <= 1.05 * TOL
+        assert_relres_matches(wl.problem.csr(vals[i]), Bm[i], X[i], rel[i], TOL)
     s.close()
+
+
+@pytest.mark.parametrize("name,precision", [("hex8_32", 2), ("q1_128", 1)])
+def test_mixed_batched_many_lanes(pkg, name, precision):
+    """The lane counts of the 3D elasticity (3x3 blocks, 32 slots, k = 30, BF16 basis) and 2D
+    diffusion (scalar, 16 slots, k = 25) workloads at moderate size: every instance through the
+    FP64 residual check, a sample of instances against the oracle."""
+    wl, Phi = _setup(name, 1)
+    P = wl.problem
+    m = wl.spec.batch
+    xis = wl.query_thetas(m)
+    Bm = wl.rhs(m)
+    phi_used = round_phi(Phi, "bf16" if precision == pkg.MIXED_BF16PHI else "f32")
+    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=precision, omega=wl.spec.omega, max_batch=m)
+    vals = [round_f32(wl.values(xi)) for xi in xis]
+    for i in range(m):
+        assert s.set_values(i, vals[i]) == pkg.OK
+    X, iters, rel, st, rc = s.solve_batch(list(range(m)), Bm, tol=TOL, maxit=5000)
+    assert rc == pkg.OK and np.all(st == pkg.OK)
+    s.close()
+    for i in range(m):
+        assert_relres_matches(P.csr(vals[i]), Bm[i], X[i], rel[i], TOL)
+    for i in sorted({0, m // 2 + 1, m - 1}):
+        ref = _oracle(wl, vals[i], phi_used, Bm[i])
+        assert ref.status == O.OK
+        assert _relerr(X[i], ref.x) <= 1e-6, (i, _relerr(X[i], ref.x))
+        assert abs(int(iters[i]) - ref.iters) <= 2, (i, iters[i], ref.iters)
 
 
 def test_result_identical_alone_and_in_mix(pkg):

@@ -43,7 +43,7 @@ def _groups(P):
 
 @pytest.mark.parametrize("name,precision,method", [("q1_32", 1, 0), ("q4_16", 1, 0), ("hex8_8", 2, 0),
                                                    ("q4_64", 1, 0), ("q1_32", 1, 1), ("q1_64", 0, 0),
-                                                   ("hex8_8", 0, 1)])
+                                                   ("hex8_8", 0, 1), ("hex8_16", 2, 0)])
 def test_sgs_matches_oracle(pkg, name, precision, method):
     wl = Workload(name)
     P, Phi = wl.problem, pod_basis(wl)

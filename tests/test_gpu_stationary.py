@@ -52,7 +52,7 @@ def test_stationary_fp64_plain_path(pkg, name):
     s.close()
 
 
-@pytest.mark.parametrize("name,precision", [("q1_32", 1), ("q4_16", 1), ("hex8_8", 2)])
+@pytest.mark.parametrize("name,precision", [("q1_32", 1), ("q4_16", 1), ("hex8_8", 2), ("hex8_16", 2)])
 def test_stationary_mixed_batched_matches_oracle(pkg, name, precision):
     wl = Workload(name)
     P, Phi = wl.problem, pod_basis(wl)
