@@ -210,3 +210,64 @@ def test_batched_torch_assembly_identical(name):
     V = wl.values_torch(xis).numpy()
     for i, xi in enumerate(xis):
         assert np.array_equal(V[i], wl.values(xi))
+
+
+# ----------------------------------------------------------------------------- multigrid snapshot solver
+@pytest.mark.parametrize("name", ["q1_16", "q4_16", "hex8_8"])
+def test_grid_operator_equals_assembled_matrix(name):
+    torch = pytest.importorskip("torch")
+    from synth import mg
+    from synth.problems import Workload
+    wl = Workload(name)
+    P = wl.problem
+    xis = wl.snapshot_thetas(2)
+    coef = torch.from_numpy(np.stack([wl.coef(x) for x in xis]))
+    A = mg.GridOperator(P.kind, P.ne, coef, torch.float64)
+    u = np.random.default_rng(0).standard_normal((2, P.n))
+    Y = mg.from_grid(P, A.apply(mg.to_grid(P, torch.from_numpy(u)))).numpy()
+    D = mg.from_grid(P, A.diagonal()).numpy()
+    for s in range(2):
+        K = P.csr(wl.values(xis[s]))
+        ref = K @ u[s]
+        assert np.abs(Y[s] - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert np.allclose(D[s], K.diagonal(), rtol=1e-14)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_restriction_is_the_transpose_of_interpolation(dim):
+    torch = pytest.importorskip("torch")
+    from synth import mg
+    rng = np.random.default_rng(dim)
+    nc = 5
+    X = torch.from_numpy(rng.standard_normal((1,) + (nc,) * dim + (2,)))
+    Y = torch.from_numpy(rng.standard_normal((1,) + (2 * nc - 1,) * dim + (2,)))
+    PX = mg.prolong(X, dim)
+    assert PX.shape == Y.shape
+    assert abs(float((PX * Y).sum()) - float((X * mg.restrict(Y, dim)).sum())) <= 1e-12 * float(
+        (PX.abs() * Y.abs()).sum())
+    # interpolation reproduces a linear field exactly
+    grid = torch.stack(torch.meshgrid(*([torch.arange(nc, dtype=torch.float64)] * dim), indexing="ij"), -1)
+    lin = (grid @ torch.arange(1.0, dim + 1, dtype=torch.float64))[None, ..., None]
+    fine = torch.stack(torch.meshgrid(*([torch.arange(2 * nc - 1, dtype=torch.float64) / 2] * dim), indexing="ij"),
+                       -1)
+    assert torch.allclose(mg.prolong(lin, dim), (fine @ torch.arange(1.0, dim + 1, dtype=torch.float64))[None, ..., None])
+
+
+@pytest.mark.parametrize("name", ["q1_32", "q4_64", "hex8_16"])
+def test_multigrid_pcg_matches_direct_solve(name):
+    torch = pytest.importorskip("torch")
+    import scipy.sparse.linalg as sla
+    from synth import mg
+    from synth.problems import Workload
+    wl = Workload(name)
+    P = wl.problem
+    xis = wl.snapshot_thetas(2)
+    coef = torch.from_numpy(np.stack([wl.coef(x) for x in xis]))
+    X, it = mg.mg_pcg(P, coef, P.f0, tol=1e-11)
+    assert it <= 40
+    for s in range(2):
+        vals = wl.values(xis[s])
+        xs = sla.splu(P.csr(vals).tocsc()).solve(P.f0)
+        assert np.linalg.norm(X[s].numpy() - xs) <= 1e-9 * np.linalg.norm(xs)
+        rel = mg.bsr_residual(P, torch.from_numpy(vals), X[s], P.f0)
+        assert rel <= 1e-10
