@@ -2,16 +2,18 @@
 """Benchmark: batched mixed-precision POD-2G-PCG on one GB300.
 
 Metric: solves/s at relative residual 1e-8 (arXiv 2207.02543, Algorithm 3 with
-the two-grid cycle of Algorithm 2, P = Phi_r). Workload: 2D plane-stress
-elasticity, Q4 elements on a 512 x 512 grid (526,338 unknowns, 2 x 2 blocks,
-left edge clamped, uniform traction on the right edge), lognormal Young's
-modulus from an 8-term KL field (mean 1, CoV 0.3), nu = 0.3, POD basis k = 20
-from 200 snapshots, a batch of 64 parameter instances sharing one pattern,
-double-float outer PCG with an FP32 preconditioner and FP32 Phi.
+the two-grid cycle of Algorithm 2, P = Phi_r). Default workload: the largest
+single-GPU configuration, 3D linear elasticity with Hex8 elements on a 128^3
+cube (6,440,067 unknowns, 57,066,625 3 x 3 blocks, z = 0 face clamped, uniform
+load on the top face), lognormal Young's modulus from a 16-term KL field (CoV
+0.4), POD basis k = 40 from 400 snapshots, a batch of 4 parameter instances under
+an HBM admission budget, double-float outer PCG with an FP32 preconditioner and
+FP32 Phi. The same line reports batch 1 of that workload, and, as extra keys, the
+2D elasticity Q4 512^2 batch-64 and 3D Hex8 64^3 batch-32 (BF16 Phi) workloads.
 
-One step = per-instance set-up of all 64 instances from FP64 values resident in
-HBM (FP32 conversion, D^-1, K_c = Phi^T K Phi, Cholesky) + the batched solve of
-all 64 to 1e-8. The inputs (4.8 GB of values) are larger than L2.
+One step = per-instance set-up of the batch from FP64 values resident in HBM
+(FP32 conversion, D^-1, K_c = Phi^T K Phi, Cholesky) + the batched solve of all
+instances to 1e-8. The inputs (16 GB of FP64 values for batch 4) are larger than L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -31,7 +33,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "q4_512"
+WORKLOAD = "hex8_128"
+EXTRAS = "q4_512,hex8_64"
+HBM_BUDGET_GB = 40.0   # admission budget of the default workload's context
 TOL = 1e-8
 MAXIT = 5000
 
@@ -148,6 +152,104 @@ def run_oracle(mode, inst, timeout=900, workload=WORKLOAD, tol=TOL, method="pcg"
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def oracle_pool(workload, workers, sample_iters, warmup, steps, tol=TOL, method="pcg", smoother="jacobi",
+                timeout=3600):
+    """`workers` single-threaded oracle processes on distinct instances (oracle.timing pool mode)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, "-m", "oracle.timing", "pool", workload, str(workers), str(sample_iters), str(warmup),
+           str(steps), str(tol), method, smoother]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+
+
+def oracle_iterations(workload, tol=TOL, method="pcg", smoother="jacobi"):
+    """Full-solve iteration counts of the oracle per query instance: from the stored file the
+    oracle-only script tests/golden/make_oracle_iterations.py writes, else one full oracle
+    solve of instance 0 (cached on disk). Returns ({instance: iterations}, source)."""
+    try:
+        g = json.load(open(GOLDEN_ITERS))[workload]
+        if g["tol"] == tol and g["method"] == method and g["smoother"] == smoother:
+            return {int(k): int(v) for k, v in g["iterations"].items()}, "tests/golden/oracle_iterations.json"
+    except (OSError, KeyError, ValueError):
+        pass
+    tag = f"{workload}_{method}_{smoother}_{fmt_tol(tol)}"
+    cache = os.path.join(ROOT, "_cache", f"oracle_{tag}_iters.json")
+    if os.path.exists(cache):
+        full = json.load(open(cache))
+    else:
+        full = run_oracle("full", 0, timeout=3600, workload=workload, tol=tol, method=method, smoother=smoother)
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        json.dump(full, open(cache, "w"))
+    return {0: int(full["iterations"])}, "a full oracle solve of instance 0"
+
+
+def host_memory_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def oracle_workers(wl, limit=None, reserve=16e9):
+    """Processes the host can run: one per core, bounded by host memory (an oracle process holds
+    its instance's CSR matrix, the basis and K Phi; its set-up peaks near 24 B per stored scalar)."""
+    P = wl.problem
+    per = 24.0 * P.nnzb * P.bs ** 2 + 24.0 * P.n * wl.spec.k + 2e8
+    avail = host_memory_available() - reserve
+    cores = os.cpu_count() or 1
+    w = cores if avail <= 0 else max(1, min(cores, int(avail // per)))
+    return min(w, limit) if limit else w
+
+
+def cpu_model():
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # noqa: BLE001
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(pool_out, iters):
+    """Solves/s of the pool: worker w finishes a solve every set-up_w + n_w * (seconds per iteration
+    of w, mean over the timed steps); n_w = the oracle's own full iteration count for w's instance,
+    or the mean of the stored counts where w's instance has none."""
+    mean_it = sum(iters.values()) / len(iters)
+    rate, used = 0.0, []
+    for w in range(pool_out["workers"]):
+        per = statistics.mean(step[w] for step in pool_out["seconds_per_iteration"])
+        n_w = iters.get(w, mean_it)
+        used.append(n_w)
+        rate += 1.0 / (pool_out["setup_s"][w] + n_w * per)
+    return rate, used
+
+
+def cpu_baseline_entry(wl, workers, sample_iters, tol, method, smoother, warmup=0, steps=1):
+    """The oracle as it stands on the host cores (a bounded sample; see oracle_rate)."""
+    out = oracle_pool(wl.spec.name, workers, sample_iters, warmup, steps, tol, method, smoother)
+    iters, src = oracle_iterations(wl.spec.name, tol, method, smoother)
+    rate, used = oracle_rate(out, iters)
+    sample = (f"{workers} single-threaded oracle processes on instances 0..{workers - 1}: each timed its "
+              f"set-up (D^-1, K_r, Cholesky; mean {statistics.mean(out['setup_s']):.1f} s) and "
+              f"{steps} x {sample_iters} {method_name(method)} iterations, scaled to a full solve by the "
+              f"oracle's iteration counts ({src}; {', '.join(f'{n:.0f}' for n in used[:8])}"
+              f"{' ...' if len(used) > 8 else ''}); host {cpu_model()}, {os.cpu_count()} cores")
+    return {"value": rate, "unit": "solves/s", "cores": workers, "kind": "oracle", "sample": sample,
+            "cpu_model": cpu_model()}, out
+
+
 def fmt_tol(tol: float) -> str:
     return f"{tol:.0e}".replace("e-0", "e-")
 
@@ -166,10 +268,18 @@ def workload_desc(wl, batch: int, tol: float) -> str:
 
 
 # ----------------------------------------------------------------------------- reference arm (oracle)
+def sample_iterations(wl):
+    """Oracle iterations per timed step: about 3 GB of single-threaded SpMV traffic (2..25)."""
+    P = wl.problem
+    per_iter = 3 * 12.0 * P.nnzb * P.bs ** 2
+    return max(2, min(25, int(3e9 // per_iter)))
+
+
 def reference_arm(args):
     """The oracle (FP64, host cores) on the GPU arm's workload, method, relaxation and tolerance:
-    one single-threaded process per core, each a bounded sample of iterations on a distinct
-    instance, scaled by the oracle's own full iteration count of instance 0."""
+    one single-threaded process per core (as many as host memory holds), each on a distinct
+    instance; per step each times a bounded sample of iterations, and a full solve's time is its
+    timed set-up plus the oracle's full iteration count times its seconds per iteration."""
     rank, world, local = _env_rank()
     if rank != 0:
         return 0
@@ -178,49 +288,24 @@ def reference_arm(args):
     wl = Workload(args.workload)
     B = args.batch or wl.spec.batch
     tol = args.tol
-    pod_basis(wl, device="cuda" if wl.n > 20_000 else None)  # cached POD basis (library snapshot solves)
-    tag = f"{args.workload}_{args.method}_{args.smoother}_{fmt_tol(tol)}"
-    cache = os.path.join(ROOT, "_cache", f"oracle_{tag}_iters.json")
-    kw = dict(workload=args.workload, tol=tol, method=args.method, smoother=args.smoother)
-    if os.path.exists(cache):
-        full = json.load(open(cache))
-    else:
-        full = run_oracle("full", 0, timeout=3600, **kw)
-        os.makedirs(os.path.dirname(cache), exist_ok=True)
-        json.dump(full, open(cache, "w"))
-    cores = min(os.cpu_count() or 1, 16)
-    sample_it = min(25, max(1, full["iterations"]))
-    from concurrent.futures import ThreadPoolExecutor
-
-    def step():
-        t0 = time.perf_counter()
-        with ThreadPoolExecutor(cores) as ex:
-            outs = list(ex.map(lambda i: run_oracle(sample_it, i, **kw), range(cores)))
-        wall = time.perf_counter() - t0
-        per_it = max(o["seconds_per_iteration"] for o in outs)
-        return wall, per_it
-    for _ in range(args.warmup):
-        step()
-    per = []
+    pod_basis(wl, device="cuda" if wl.n > 20_000 else None)  # the POD basis, cached on disk for the pool
+    workers = oracle_workers(wl, limit=args.oracle_workers or None)
+    sample_it = sample_iterations(wl)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        per.append(step()[1])
-    wall = time.perf_counter() - t0
-    per_it = statistics.mean(per)
-    value = cores / (per_it * max(full["iterations"], 1))
+    cpu, out = cpu_baseline_entry(wl, workers, sample_it, tol, args.method, args.smoother, warmup=args.warmup,
+                                  steps=args.steps)
+    value = cpu["value"]
     line = {
         "metric": f"solves/s at rel. residual {fmt_tol(tol)} (batched {method_name(args.method)})",
         "value": value, "unit": "solves/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(out["step_wall_s"]) * 1e3 if out["step_wall_s"] else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
         "config": {"workload": workload_desc(wl, B, tol), "method": method_name(args.method),
-                   "smoother": args.smoother, "batch": B, "n": wl.problem.n, "k": wl.spec.k},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{cores} single-threaded oracle processes, {sample_it} "
-                                   f"{method_name(args.method)} iterations each on distinct instances per step, "
-                                   f"scaled by the oracle's full iteration count ({full['iterations']}) for "
-                                   f"instance 0"},
+                   "smoother": args.smoother, "batch": B, "n": wl.problem.n, "k": wl.spec.k,
+                   "oracle_prepare_s": round(out["prepare_s"], 1), "wall_s": round(time.perf_counter() - t0, 1)},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -249,8 +334,163 @@ def job_value(ms_max: float, world: int, batch: int) -> float:
 
 
 # ----------------------------------------------------------------------------- GB300 arm
+class WorkloadRun:
+    """One workload on this rank: its POD basis, B instances' FP64 inputs resident in HBM, and a
+    solver context (optionally under an HBM admission budget)."""
+
+    def __init__(self, args, pkg, name, B, rank=0, hbm_budget=0, autotune=True):
+        import torch
+        from synth.problems import Workload
+        from synth.snapshots import pod_basis
+        self.pkg, self.args = pkg, args
+        self.wl = wl = Workload(name)
+        P = self.P = wl.problem
+        self.B = B
+        t0 = time.time()
+        self.Phi = pod_basis(wl, device="cuda")
+        self.t_phi = time.time() - t0
+        self.xis = wl.query_thetas(B, offset=replica_offset(rank, B))   # distinct instances per rank
+        self.elements = args.operator == "elements"
+        if self.elements:   # FP64 element coefficients, resident in HBM
+            self.vals = torch.from_numpy(np.stack([wl.coef(xi) for xi in self.xis])).cuda()
+        else:               # FP64 assembled values, resident in HBM
+            self.vals = wl.values_torch(self.xis, device="cuda").reshape(B, -1).contiguous()
+        self.b_dev = torch.from_numpy(wl.rhs(B, offset=replica_offset(rank, B))).cuda()
+        self.x_dev = torch.empty_like(self.b_dev)
+        self.stream = torch.cuda.Stream()
+        precision = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
+        self.method = pkg.STATIONARY if args.method == "stationary" else pkg.PCG
+        self.smoother = pkg.SMOOTHER_SGS if args.smoother == "sgs" else pkg.SMOOTHER_JACOBI
+        el = (dict(conn=P.conn, k_ref=P.Kref, fixed=P.clamped if P.dirichlet == "identity" else None)
+              if self.elements else None)
+        self.s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, self.Phi, precision=precision, omega=wl.spec.omega,
+                            max_batch=B, stream=self.stream.cuda_stream, method=self.method, elements=el,
+                            smoother=self.smoother, hbm_budget=int(hbm_budget))
+        self.slots = list(range(B))
+        self.set_batch = self.s.set_coeffs_batch_dev if self.elements else self.s.set_values_batch_dev
+        self.set_one = self.s.set_coeffs if self.elements else self.s.set_values
+        self.x0_dev = torch.empty_like(self.b_dev) if args.x0 == "rom" else None
+        self.tuning = None
+        if args.tuning:
+            # a given launch shape (e.g. the one an earlier autotuned run reported), no autotuning
+            shape = {f"grid_{k}": int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))}
+            assert self.s.set_tuning(**shape) == pkg.OK, shape
+            self.tuning = self.s.get_tuning()
+        elif autotune and not args.no_autotune:
+            # launch shapes picked by timing candidates on this workload (outside the timed region)
+            st, _ = self.set_batch(self.slots, self.vals)
+            assert st == pkg.OK, pkg.strerror(st)
+            st, self.tuning = self.s.autotune(self.slots, self.b_dev, iters=32)
+            assert st == pkg.OK, pkg.strerror(st)
+
+    def step(self):
+        pkg, s = self.pkg, self.s
+        st, _ = self.set_batch(self.slots, self.vals)
+        assert st == pkg.OK, pkg.strerror(st)
+        if self.x0_dev is not None:   # POD reduced-order solution as the initial guess
+            st = s.rom_solution_dev(self.slots, self.b_dev, self.x0_dev)
+            assert st == pkg.OK, pkg.strerror(st)
+        iters, rel, status, rc = s.solve_batch_dev(self.slots, self.b_dev, self.x_dev, x0_dev=self.x0_dev,
+                                                   tol=self.args.tol, maxit=self.args.maxit)
+        assert rc == pkg.OK, (pkg.strerror(rc), status)
+        return iters, rel
+
+    def timed(self, steps, warmup, dist=None, sampler=None):
+        """warmup untimed steps, then `steps` steps between CUDA events on the solver's stream."""
+        import torch
+        for _ in range(max(warmup, 0)):
+            self.step()
+        l0 = self.s.launch_count()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(self.stream)
+        its, rels = [], []
+        for _ in range(steps):
+            it, rel = self.step()
+            its.append(it)
+            rels.append(rel)
+        ev1.record(self.stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        if dist:
+            dist.barrier()
+        return dict(ms=ev0.elapsed_time(ev1) / steps, iters=np.concatenate(its), relres=np.concatenate(rels),
+                    launches=self.s.launch_count() - l0, clocks=clocks)
+
+    def roofline(self, steps, num_sms):
+        """Per-kernel CUDA-event times from separate instrumented steps (event-record nodes inside the
+        graph, outside the timed region), and algorithmic bytes / time per kernel."""
+        import torch
+        s, wl, P, B = self.s, self.wl, self.P, self.B
+        s.kernel_timing(True)
+        lane_iters = 0
+        for _ in range(max(1, steps)):
+            iters, _ = self.step()
+            lane_iters += int(np.sum(iters))
+        torch.cuda.synchronize()
+        ktimes = s.kernel_times()
+        s.kernel_timing(False)
+        peaks, peak_kind = measured_peaks()
+        Bp = 1 << (B - 1).bit_length()
+        tun = s.get_tuning() or {}
+        G = tun.get("grid_rows", max(1, min((P.n_nodes * Bp + 255) // 256, 4 * num_sms)))
+        kp = {0: 0}.get(wl.spec.k, [v for v in (0, 8, 16, 24, 32, 40, 48, 64) if v >= wl.spec.k][0])
+        nl = {k: v[1] for k, v in ktimes.items()}
+        sgs = self.args.smoother == "sgs"
+        kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp, self.elements, sgs)
+        # the same bytes with every lane active in every launch (what one ncu capture of a launch sees)
+        kb_all = kernel_bytes(wl, kp, B, 1, G, Bp, self.elements, sgs)
+        rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
+        dom = max(ktimes, key=lambda k: ktimes[k][0])
+        tot_k = sum(v[0] for v in ktimes.values())
+        key = (wl.spec.name, B, self.args.operator)
+        row = ("k_spmv", "k_smooth1", "k_post")
+        return {"bound": "hbm", "kernel": dom, "achieved": rates[dom], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": rates[dom] / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                "bytes_per_launch": kb[dom] / max(nl[dom], 1),
+                "bytes_per_launch_all_lanes": kb_all[dom],
+                "ms_per_launch": ktimes[dom][0] / max(nl[dom], 1),
+                "traffic": NCU_TRAFFIC.get(key, {}).get(dom),
+                "traffic_source": NCU_SOURCE.get(key),
+                "frac_vs_8TBs": rates[dom] / 8000.0,
+                "all_kernels": {k: {"share": ktimes[k][0] / tot_k, "GBs": round(rates[k], 1),
+                                    "ms_per_launch": ktimes[k][0] / max(nl[k], 1)} for k in ktimes},
+                "spmv_smoother_GBs": sum(kb[k] for k in row) / (sum(ktimes[k][0] for k in row) / 1e3) / 1e9,
+                "spmv_smoother_frac": sum(kb[k] for k in row) / (sum(ktimes[k][0] for k in row) / 1e3) / 1e9
+                / peaks["hbm_gbs"]}
+
+    def setup_ms(self):
+        import torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        st, _ = self.set_batch(self.slots, self.vals)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        assert st == self.pkg.OK
+        return e0.elapsed_time(e1)
+
+    def close(self):
+        import torch
+        self.s.close()
+        del self.vals, self.b_dev, self.x_dev
+        torch.cuda.empty_cache()
+
+
+def workload_summary(run, t, roof, B):
+    return {"workload": workload_desc(run.wl, B, run.args.tol), "batch": B, "value": B / (t["ms"] / 1e3),
+            "unit": "solves/s", "ms_per_step": t["ms"], "iters_mean": float(np.mean(t["iters"])),
+            "iters_max": int(np.max(t["iters"])), "relres_max": float(np.max(t["relres"])),
+            "tuning": run.tuning, "phi_setup_s": round(run.t_phi, 1),
+            "roofline": {k: roof[k] for k in ("kernel", "achieved", "frac", "ms_per_launch", "spmv_smoother_GBs",
+                                              "spmv_smoother_frac")},
+            "kernels_GBs": {k: v["GBs"] for k, v in roof["all_kernels"].items()}}
+
+
 def gb300_arm(args):
-    import numpy as np
     import torch
     rank, world, local = _env_rank()
     torch.cuda.set_device(local)
@@ -261,206 +501,112 @@ def gb300_arm(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2207_02543_gb300 as pkg
-    from synth.problems import Workload
-    from synth.snapshots import pod_basis
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
 
-    wl = Workload(args.workload)
-    P = wl.problem
-    B = args.batch or wl.spec.batch
-    t0 = time.time()
-    Phi = pod_basis(wl, device="cuda")
-    t_phi = time.time() - t0
-    # instances of this replica: distinct per rank
-    xis = wl.query_thetas(B, offset=replica_offset(rank, B))
-    elements = args.operator == "elements"
-    if elements:   # FP64 element coefficients, resident in HBM
-        vals = torch.from_numpy(np.stack([wl.coef(xi) for xi in xis])).cuda()
-    else:          # FP64 assembled values, resident in HBM
-        vals = wl.values_torch(xis, device="cuda").reshape(B, -1).contiguous()
-    b_dev = torch.from_numpy(wl.rhs(B, offset=replica_offset(rank, B))).cuda()
-    x_dev = torch.empty_like(b_dev)
-    stream = torch.cuda.Stream()
-    precision = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
-    method = pkg.STATIONARY if args.method == "stationary" else pkg.PCG
-    tol, maxit = args.tol, args.maxit
-    el = dict(conn=P.conn, k_ref=P.Kref, fixed=P.clamped if P.dirichlet == "identity" else None) if elements else None
-    smoother = pkg.SMOOTHER_SGS if args.smoother == "sgs" else pkg.SMOOTHER_JACOBI
-    s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=precision, omega=wl.spec.omega,
-                   max_batch=B, stream=stream.cuda_stream, method=method, elements=el, smoother=smoother)
-    slots = list(range(B))
-    set_batch = s.set_coeffs_batch_dev if elements else s.set_values_batch_dev
-    set_one = s.set_coeffs if elements else s.set_values
-
-    x0_dev = torch.empty_like(b_dev) if args.x0 == "rom" else None
-
-    def step():
-        st, sts = set_batch(slots, vals)
-        assert st == pkg.OK, pkg.strerror(st)
-        if x0_dev is not None:   # POD reduced-order solution as the initial guess
-            st = s.rom_solution_dev(slots, b_dev, x0_dev)
-            assert st == pkg.OK, pkg.strerror(st)
-        iters, rel, status, rc = s.solve_batch_dev(slots, b_dev, x_dev, x0_dev=x0_dev, tol=tol, maxit=maxit)
-        assert rc == pkg.OK, (pkg.strerror(rc), status)
-        return iters, rel
-
-    tuning = None
-    if args.tuning:
-        # a given launch shape (e.g. the one an earlier autotuned run reported), no autotuning
-        shape = {f"grid_{k}": int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))}
-        assert s.set_tuning(**shape) == pkg.OK, shape
-        tuning = s.get_tuning()
-    elif not args.no_autotune:
-        # launch shapes picked by timing candidates on this workload (outside the timed region)
-        st, sts = set_batch(slots, vals)
-        assert st == pkg.OK, pkg.strerror(st)
-        st, tuning = s.autotune(slots, b_dev, iters=32)
-        assert st == pkg.OK, pkg.strerror(st)
-    torch.cuda.synchronize()
-    for _ in range(max(args.warmup, 0)):
-        iters, rel = step()
+    from synth.problems import SPECS
+    B = args.batch or SPECS[args.workload].batch
+    budget = args.hbm_budget_gb * 1e9 if args.workload == WORKLOAD else 0
+    run = WorkloadRun(args, pkg, args.workload, B, rank, hbm_budget=budget)
+    wl, P = run.wl, run.P
     sampler = ClockSampler(local)
-    l0 = s.launch_count()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    lane_iters = 0
-    for _ in range(args.steps):
-        iters, rel = step()
-        lane_iters += int(np.sum(iters))
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    launches = s.launch_count() - l0
-    # per-kernel CUDA-event times: separate, instrumented steps (event-record nodes
-    # inside the graph), outside the timed region above
-    s.kernel_timing(True)
-    lane_iters = 0
-    for _ in range(max(1, min(args.steps, 2))):
-        iters, rel = step()
-        lane_iters += int(np.sum(iters))
-    torch.cuda.synchronize()
-    ktimes = s.kernel_times()
-    s.kernel_timing(False)
-    # per-instance set-up (values or coefficients -> D^-1, K_c and its Cholesky factor) on its own
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    st, _ = set_batch(slots, vals)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    assert st == pkg.OK
-    setup_ms = e0.elapsed_time(e1)
-    ms = max_over_ranks(ms, dist)
+    t = run.timed(args.steps, args.warmup, dist, sampler)
+    roofline = run.roofline(min(args.steps, 2), num_sms)
+    setup_ms = run.setup_ms()
+    ms = max_over_ranks(t["ms"], dist)
     value = job_value(ms, world, B)
-
-    # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
-    peaks, peak_kind = measured_peaks()
-    Bp = 1 << (B - 1).bit_length()
-    G = max(1, min((P.n_nodes * Bp + 255) // 256, 4 * torch.cuda.get_device_properties(local).multi_processor_count))
-    kp = {0: 0}.get(wl.spec.k, [v for v in (0, 8, 16, 24, 32, 40, 48, 64) if v >= wl.spec.k][0])
-    nl = {k: v[1] for k, v in ktimes.items()}
-    kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp, elements, args.smoother == "sgs")
-    rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
-    dom = max(ktimes, key=lambda k: ktimes[k][0])
-    tot_k = sum(v[0] for v in ktimes.values())
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": rates[dom], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": rates[dom] / peaks["hbm_gbs"], "peak_kind": peak_kind,
-                "bytes_per_launch": kb[dom] / max(nl[dom], 1),
-                "ms_per_launch": ktimes[dom][0] / max(nl[dom], 1),
-                "traffic": NCU_TRAFFIC.get((args.workload, B, args.operator), {}).get(dom),
-                "traffic_source": NCU_SOURCE.get((args.workload, B, args.operator)),
-                "frac_vs_8TBs": rates[dom] / 8000.0,
-                "all_kernels": {k: {"share": ktimes[k][0] / tot_k, "GBs": round(rates[k], 1),
-                                    "ms_per_launch": ktimes[k][0] / max(nl[k], 1)} for k in ktimes},
-                "spmv_smoother_GBs": (kb["k_spmv"] + kb["k_smooth1"] + kb["k_post"]) /
-                                     ((ktimes["k_spmv"][0] + ktimes["k_smooth1"][0] + ktimes["k_post"][0]) / 1e3) / 1e9}
+    device_bytes = run.s.device_bytes()
 
     extra = {}
     if rank == 0 and world == 1:
+        s, slots, tol, maxit = run.s, run.slots, args.tol, args.maxit
         # end to end through the C ABI with host buffers (values, b in; x out)
-        vals_h = vals.cpu().numpy()
-        b_h = b_dev.cpu().numpy()
+        vals_h = run.vals.cpu().numpy()
+        b_h = run.b_dev.cpu().numpy()
         e2e_steps = max(1, min(args.steps, 2))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             for i in slots:
-                assert set_one(i, vals_h[i]) == pkg.OK
-            if x0_dev is None:
+                assert run.set_one(i, vals_h[i]) == pkg.OK
+            if run.x0_dev is None:
                 X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=tol, maxit=maxit)
             else:   # the reduced-order initial guess lives on the device: copy b in, x out
-                bd = torch.from_numpy(b_h).to(b_dev.device)
-                assert s.rom_solution_dev(slots, bd, x0_dev) == pkg.OK
-                it_h, rel_h, st_h, rc = s.solve_batch_dev(slots, bd, x_dev, x0_dev=x0_dev, tol=tol, maxit=maxit)
-                X = x_dev.cpu().numpy()
+                bd = torch.from_numpy(b_h).to(run.b_dev.device)
+                assert s.rom_solution_dev(slots, bd, run.x0_dev) == pkg.OK
+                it_h, rel_h, st_h, rc = s.solve_batch_dev(slots, bd, run.x_dev, x0_dev=run.x0_dev, tol=tol,
+                                                          maxit=maxit)
+                X = run.x_dev.cpu().numpy()
             assert rc == pkg.OK
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         extra["e2e"] = {"value": B / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(vals_h.nbytes + b_h.nbytes),
                         "d2h_bytes_per_step": int(X.nbytes)}
         # plain FP64 one-at-a-time baseline on the same GPU
         if not args.no_plain:
-            sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1,
-                            method=method, smoother=smoother)
-            vals_plain = vals if not elements else wl.values_torch(xis[:2], device="cuda").reshape(2, -1)
-            nplain = 2
-            times, its = [], []
-            for i in range(nplain):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                assert sp.set_values(0, vals_plain[i]) == pkg.OK
-                xp, itp, relp, stp = sp.solve(0, b_h[i], tol=tol, maxit=maxit)
-                torch.cuda.synchronize()
-                times.append(time.perf_counter() - t0)
-                its.append(itp)
-                assert stp == pkg.OK
-            sp.close()
-            extra["plain_fp64"] = {"value": 1.0 / statistics.mean(times), "unit": "solves/s",
-                                   "iters": its, "ratio_batched_over_plain": value / (1.0 / statistics.mean(times))}
-        # serving: Poisson arrivals at ~70% of the batched throughput, continuous batching
-        if not args.no_serve:
-            loads = [float(v) for v in args.serve_loads.split(",")]
-            runs = [dict(serve_latency(s, pkg, wl, vals_h, b_h, rate=f * value, nreq=args.serve_requests, tol=tol,
-                                       maxit=maxit), load=f) for f in loads]
-            extra["serving"] = runs[0]
-            if len(runs) > 1:
-                extra["serving_loads"] = runs
-        # CPU baseline: the oracle on a bounded sample (single thread)
+            extra["plain_fp64"] = plain_baseline(run, pkg, vals_h, b_h, value, num_sms)
+        # serving: Poisson arrivals at a fraction of the batched throughput, continuous batching
+        # (requests carry their instance's values from host memory: measured here on workloads
+        # whose instances are below 1 GB, otherwise on the first such extra workload)
+        serve_here = not args.no_serve and vals_h[0].nbytes <= 1e9
+        if serve_here:
+            extra.update(serving_entry(args, s, pkg, wl, vals_h, b_h, value))
+        del vals_h, X
+        # the same workload at batch 1
+        if B > 1 and not args.no_batch1:
+            run.close()
+            r1 = WorkloadRun(args, pkg, args.workload, 1, rank, hbm_budget=budget)
+            t1 = r1.timed(max(1, min(args.steps, 3)), 1)
+            extra["batch1"] = workload_summary(r1, t1, r1.roofline(1, num_sms), 1)
+            r1.close()
+        else:
+            run.close()
+        # the other configurations, each a few steps in its own context
+        extras = [w for w in args.extras.split(",") if w and w != args.workload]
+        if extras:
+            extra["extra_workloads"] = {}
+        for name in extras:
+            Bx = SPECS[name].batch
+            rx = WorkloadRun(args, pkg, name, Bx, rank)
+            tx = rx.timed(2, 2)
+            sx = workload_summary(rx, tx, rx.roofline(1, num_sms), Bx)
+            extra["extra_workloads"][f"{name}_b{Bx}"] = sx
+            if not args.no_serve and "serving" not in extra and rx.vals[0].numel() * 8 <= 1e9:
+                vh, bh = rx.vals.cpu().numpy(), rx.b_dev.cpu().numpy()
+                extra.update(serving_entry(args, rx.s, pkg, rx.wl, vh, bh, sx["value"]))
+                extra["serving"]["workload"] = sx["workload"]
+                del vh, bh
+            rx.close()
+        # CPU baseline: the oracle on the host cores, a bounded sample
         if not args.no_cpu:
             try:
-                o = run_oracle(100, 0, workload=args.workload, tol=tol, method=args.method, smoother=args.smoother)
-                it_full = int(iters[0])
-                cpu_val = 1.0 / (o["seconds_per_iteration"] * it_full)
-                extra["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                         "sample": f"instance 0, first 100 {method_name(args.method)} iterations of "
-                                                   f"the FP64 oracle (one thread), scaled by the instance's "
-                                                   f"iteration count {it_full}"}
+                import resource
+                rss = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss * 1024
+                workers = oracle_workers(wl, limit=args.oracle_workers or None, reserve=16e9 + rss)
+                extra["cpu_baseline"], _ = cpu_baseline_entry(wl, workers, sample_iterations(wl), tol, args.method,
+                                                              args.smoother)
             except Exception as e:  # noqa: BLE001
-                extra["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                         "sample": f"failed: {e}"[:200]}
-    s.close()
+                extra["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 0, "kind": "oracle",
+                                         "sample": f"failed: {e}"[:300]}
+    else:
+        run.close()
     if rank == 0:
         line = {
-            "metric": f"solves/s at rel. residual {fmt_tol(tol)} (batched {method_name(args.method)})",
+            "metric": f"solves/s at rel. residual {fmt_tol(args.tol)} (batched {method_name(args.method)})",
             "value": value, "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
-            "config": {"workload": workload_desc(wl, B, tol), "method": method_name(args.method),
-                       "operator": args.operator, "smoother": args.smoother, "x0": args.x0, "tuning": tuning,
+            "config": {"workload": workload_desc(wl, B, args.tol), "method": method_name(args.method),
+                       "operator": args.operator, "smoother": args.smoother, "x0": args.x0, "tuning": run.tuning,
                        "batch": B, "n": P.n, "nnzb": P.nnzb, "k": wl.spec.k, "parallelism": f"replicas{world}",
-                       "l2": (f"inputs larger than L2 ({vals.numel() * 8 / 1e9:.2f} GB FP64 "
-                              f"{'coefficients' if elements else 'values'} per step; per-iteration working set "
-                              f"{P.n * B * 8 * 5 / 1e9:.2f} GB of vectors)"),
-                       "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
-                       "relres_max": float(np.max(rel)), "phi_setup_s": round(t_phi, 1),
+                       "hbm_budget_bytes": int(budget), "device_bytes": int(device_bytes),
+                       "l2": (f"inputs larger than L2 ({B * run.P.nnzb * P.bs ** 2 * 8 / 1e9:.2f} GB FP64 "
+                              f"{'coefficients' if run.elements else 'values'} per step; per-iteration working "
+                              f"set {P.n * B * 8 * 5 / 1e9:.2f} GB of vectors)"),
+                       "iters_mean": float(np.mean(t["iters"])), "iters_max": int(np.max(t["iters"])),
+                       "relres_max": float(np.max(t["relres"])), "phi_setup_s": round(run.t_phi, 1),
                        "setup_ms_per_step": round(setup_ms, 2)},
-            "gpu_launches": int(launches / max(args.steps, 1)) if args.steps else 0,
-            "roofline": roofline, "clocks": clocks,
+            "gpu_launches": int(t["launches"] / max(args.steps, 1)) if args.steps else 0,
+            "roofline": roofline, "clocks": t["clocks"],
         }
         line.update(extra)
         line.setdefault("cpu_baseline", None)
@@ -469,6 +615,48 @@ def gb300_arm(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def serving_entry(args, s, pkg, wl, vals_h, b_h, value):
+    loads = [float(v) for v in args.serve_loads.split(",")]
+    nreq = args.serve_requests or max(8, min(128, int(30 * value)))
+    runs = [dict(serve_latency(s, pkg, wl, vals_h, b_h, rate=f * value, nreq=nreq, tol=args.tol,
+                               maxit=args.maxit), load=f) for f in loads]
+    out = {"serving": runs[0]}
+    if len(runs) > 1:
+        out["serving_loads"] = runs
+    return out
+
+
+def plain_baseline(run, pkg, vals_h, b_h, value, num_sms):
+    """The plain path (FP64 values, vectors and basis; one instance at a time, kernel by kernel,
+    convergence checked on the host every iteration, no graphs) on two of the instances."""
+    import torch
+    wl, P = run.wl, run.P
+    sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, run.Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1,
+                    method=run.method, smoother=run.smoother)
+    vals_plain = run.vals if not run.elements else wl.values_torch(run.xis[:2], device="cuda").reshape(2, -1)
+    times, its = [], []
+    for i in range(min(2, run.B)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        assert sp.set_values(0, vals_plain[i]) == pkg.OK
+        xp, itp, relp, stp = sp.solve(0, b_h[i], tol=run.args.tol, maxit=run.args.maxit)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        its.append(itp)
+        assert stp == pkg.OK
+    sp.close()
+    pv = 1.0 / statistics.mean(times)
+    # algorithmic bytes of one plain iteration (FP64 values read by 3 SpMVs, ~13 FP64 vector streams,
+    # Phi twice) and the bytes bound of the batched/plain ratio
+    n, nnz, k = P.n, P.nnzb * P.bs ** 2, wl.spec.k
+    plain_iter = 3 * (8 * nnz + 4 * nnz) + 8 * 13 * n + 2 * 8 * n * k
+    it_mean = statistics.mean(its)
+    per_solve = [t for t in times]
+    return {"value": pv, "unit": "solves/s", "iters": its, "ratio_batched_over_plain": value / pv,
+            "achieved_GBs": plain_iter * it_mean / statistics.mean(per_solve) / 1e9,
+            "bytes_per_iteration": plain_iter}
 
 
 def serve_latency(s, pkg, wl, vals_h, b_h, rate, nreq, tol=TOL, maxit=MAXIT):
@@ -512,7 +700,11 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=128)
+    ap.add_argument("--serve-requests", type=int, default=0, help="requests per serving load (default: ~30 s of work)")
+    ap.add_argument("--no-batch1", action="store_true", help="skip the batch-1 line of the workload")
+    ap.add_argument("--extras", default=EXTRAS, help="other workloads measured after the main one (comma list)")
+    ap.add_argument("--hbm-budget-gb", type=float, default=HBM_BUDGET_GB,
+                    help="HBM admission budget of the default workload's context")
     ap.add_argument("--serve-loads", default="0.7",
                     help="Poisson arrival rates as fractions of the measured batch throughput, e.g. 0.5,0.7,0.9")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling of smaller cases)")
@@ -529,6 +721,8 @@ def main():
     ap.add_argument("--x0", default="zero", choices=["zero", "rom"],
                     help="initial guess: zero, or the POD reduced-order solution Phi K_c^-1 Phi^T b")
     ap.add_argument("--tol", type=float, default=TOL)
+    ap.add_argument("--oracle-workers", type=int, default=0,
+                    help="cap on the oracle processes of the CPU baseline (default: cores, bounded by host memory)")
     ap.add_argument("--maxit", type=int, default=MAXIT)
     args = ap.parse_args()
     if args.impl == "reference":
