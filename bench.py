@@ -30,6 +30,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -373,7 +375,8 @@ class WorkloadRun:
         self.tuning = None
         if args.tuning:
             # a given launch shape (e.g. the one an earlier autotuned run reported), no autotuning
-            shape = {f"grid_{k}": int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))}
+            shape = {(k if k == "rows_kernel" else f"grid_{k}"): int(v)
+                     for k, v in (kv.split("=") for kv in args.tuning.split(","))}
             assert self.s.set_tuning(**shape) == pkg.OK, shape
             self.tuning = self.s.get_tuning()
         elif autotune and not args.no_autotune:
