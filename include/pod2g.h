@@ -86,6 +86,14 @@ extern "C" {
                                     forward sweeps before, backward sweeps after the coarse
                                     correction (omega is not used) */
 
+/* contraction K_c = Phi^T (K Phi) of the per-instance set-up on the mixed paths (K Phi is
+ * always formed in double-float on the CUDA cores) */
+#define POD2G_COARSE_DF      0  /* double-float on the CUDA cores (~14 significant digits) */
+#define POD2G_COARSE_TENSOR  1  /* tensor cores (tcgen05, BF16 operands, FP32 accumulation): each
+                                   operand split into three BF16 pieces, the six products whose
+                                   pieces reach down to ~2^-24 of the term, FP32 partial sums per
+                                   CTA added in FP64 (K_c to ~1e-7 of its largest entry) */
+
 /* solution methods */
 #define POD2G_PCG            0  /* PCG preconditioned by one POD-2G cycle from zero (Algorithm 3) */
 #define POD2G_STATIONARY     1  /* the POD-2G two-grid cycle itself as the iteration (Algorithm 2,
@@ -110,7 +118,10 @@ typedef struct {
     int beta_pr;              /* 0: beta = r_{k+1}^T s_{k+1} / r_k^T s_k (Algorithm 1); 1: Polak-Ribiere */
     int max_batch;            /* number of instance slots (1..256) */
     size_t hbm_budget;        /* bytes the context may allocate; 0 = no limit */
-    int64_t spin_limit;       /* bound on host polling iterations of a solve (0 = default) */
+    int64_t spin_limit;       /* bound on the host's polls of a batched solve (one poll per CUDA-graph
+                                 launch of `chunk` iterations; 0 = maxit / chunk + 2). When it runs
+                                 out, the unfinished instances stop with status POD2G_TIMEOUT and
+                                 their last iterate; the context stays usable. */
     int chunk;                /* PCG iterations per CUDA-graph launch in the batched path (default 8) */
     void* stream;             /* cudaStream_t to run on; NULL = a stream owned by the context */
     int method;               /* POD2G_PCG (default) or POD2G_STATIONARY; iters then counts cycles */
@@ -119,6 +130,8 @@ typedef struct {
                                  neighbour holds); a sweep visits colour 0, 1, .. and within a node
                                  its components in order (backward: all reversed). Mixed precision
                                  with SGS: beta_pr must be 0. */
+    int coarse;               /* POD2G_COARSE_TENSOR (default) or POD2G_COARSE_DF: how the mixed
+                                 paths contract K_c = Phi^T (K Phi); ignored by POD2G_FP64 */
 } pod2g_opts;
 
 /* Fill *opts with defaults. Never fails. */
@@ -272,6 +285,34 @@ int64_t pod2g_device_bytes(pod2g_t ctx);
 int pod2g_kernel_timing(pod2g_t ctx, int on);
 int pod2g_kernel_times(pod2g_t ctx, double* ms, int64_t* launches);
 
+/* The coarse matrix of a set-up slot (Section 3.3, eq. POD_ROM): copies its k x k
+ * lower-triangular Cholesky factor L, K_c = L L^T with K_c = (Phi^T K Phi +
+ * (Phi^T K Phi)^T) / 2, row-major into L (host, k*k doubles; the strict upper triangle
+ * is zero). POD2G_INVALID_ARG for a slot without a valid set-up. */
+int pod2g_coarse_factor(pod2g_t ctx, int slot, double* L);
+
+/* ---- Surrogate initial guess (Section 3.2): u_sur(theta) = s * decoder(FFNN(theta)).
+ * FFNN: h1 = tanh(W1 theta + b1), h2 = tanh(W2 h1 + b2), o = W3 h2 + b3 (FP64 on the device),
+ * latent z = z_mean + z_std * o; decoder: u = Psi z with ks modes Psi (stored in FP32, the
+ * product accumulated in FP32); s = the query's load factor. The solver accepts any x0: pass the
+ * prediction as x0_dev of pod2g_solve_batch_dev. The object is independent of any solver
+ * context. */
+typedef struct pod2g_sur* pod2g_sur_t;
+/* Copies all arrays (host): psi [n x ks] column-major; w1 [hidden x m], w2 [hidden x hidden],
+ * w3 [ks x hidden] row-major; b1, b2 [hidden]; b3, z_mean, z_std [ks]. Limits: 1 <= m <= 64,
+ * 1 <= hidden <= 256, 1 <= ks <= 256 (POD2G_INVALID_ARG otherwise). stream: the cudaStream_t the
+ * predictions run in (NULL = a stream owned by the object). */
+int pod2g_surrogate_create(int64_t n, int m, int ks, int hidden, const double* psi, const double* w1,
+                           const double* b1, const double* w2, const double* b2, const double* w3,
+                           const double* b3, const double* z_mean, const double* z_std, void* stream,
+                           pod2g_sur_t* out);
+/* x_dev (device, nq consecutive vectors of n doubles) = the predictions for theta (host, nq x m
+ * row-major) and scale (host, nq load factors; NULL = 1). Queued in the object's stream; returns
+ * once queued (the host arrays may be reused at return). */
+int pod2g_surrogate_predict_dev(pod2g_sur_t sur, int nq, const double* theta, const double* scale,
+                                double* x_dev);
+void pod2g_surrogate_destroy(pod2g_sur_t sur);
+
 /* Free all device memory of the context. NULL is ignored. */
 void pod2g_destroy(pod2g_t ctx);
 
@@ -326,16 +367,23 @@ typedef struct {
     int32_t grid_prol;      /* prolongation: 1..8*SMs */
     int32_t grid_vec;       /* vector updates (p; x and r): 1..8*SMs */
     int32_t grid_spmv;      /* outer SpMV q = K p: multiple of 8, 8..8*SMs */
+    int32_t rows_kernel;    /* form of the sparse row kernels: bit 0 the smoother passes, bit 1 the
+                               outer SpMV use the warp-staged kernels (each warp copies the matrix
+                               values of its rows into shared memory with bulk asynchronous copies
+                               ahead of use); 0 = one thread per block row and slot. Non-zero only
+                               for assembled operators with 4..64 slot lanes and Jacobi relaxation
+                               (default there: 3). */
 } pod2g_tuning;
 
 /* Current shape (mixed contexts; FP64 contexts return POD2G_INVALID_ARG). */
 int pod2g_get_tuning(pod2g_t ctx, pod2g_tuning* out);
 /* Set a shape; POD2G_INVALID_ARG if a field is out of range or the context is serving. */
 int pod2g_set_tuning(pod2g_t ctx, const pod2g_tuning* t);
-/* Autotuner: for five candidate shapes, solve the given set-up slots with right-hand
+/* Autotuner: for five candidate shapes (and, where they apply, five grid sizes of the
+ * warp-staged row kernels), solve the given set-up slots with right-hand
  * sides b_dev (nslots consecutive vectors of n doubles, device) for `iters`
  * iterations (rounded up to whole graph launches), timing each kernel with CUDA
- * events, and keep per kernel group the fastest candidate. The slots are left idle
+ * events, and keep per kernel group the fastest candidate (kernel form and grid). The slots are left idle
  * (their set-up stays valid). *out (may be NULL) receives the chosen shape. Not
  * while serving. */
 int pod2g_autotune(pod2g_t ctx, int nslots, const int* slots, const double* b_dev, int iters,

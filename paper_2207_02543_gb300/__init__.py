@@ -27,7 +27,9 @@ EXPORTS = [
     "pod2g_destroy", "pod2g_strerror", "pod2g_solve_noalloc", "pod2g_device_bytes", "pod2g_create_elements",
     "pod2g_set_coeffs", "pod2g_set_coeffs_batch_dev", "pod2g_get_tuning", "pod2g_set_tuning", "pod2g_autotune",
     "pod2g_rom_solution_dev", "pod2g_set_field", "pod2g_set_theta", "pod2g_set_theta_batch", "pod2g_submit_theta",
+    "pod2g_coarse_factor", "pod2g_surrogate_create", "pod2g_surrogate_predict_dev", "pod2g_surrogate_destroy",
 ]
+COARSE_DF, COARSE_TENSOR = 0, 1  # K_c contraction of the mixed paths: double-float CUDA cores, or tensor cores
 NOALLOC_MAX_N, NOALLOC_MAX_K = 16384, 32
 TOO_LARGE = 11
 KERNEL_NAMES = ["k_p", "k_spmv", "k_upd", "k_smooth1", "k_restrict", "k_coarse", "k_prol", "k_post"]
@@ -45,14 +47,14 @@ class Elements(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("grid_rows", C.c_int32), ("grid_restrict", C.c_int32), ("grid_prol", C.c_int32),
-                ("grid_vec", C.c_int32), ("grid_spmv", C.c_int32)]
+                ("grid_vec", C.c_int32), ("grid_spmv", C.c_int32), ("rows_kernel", C.c_int32)]
 
 
 class Opts(C.Structure):
     _fields_ = [("omega", C.c_double), ("pre", C.c_int), ("post", C.c_int), ("precision", C.c_int),
                 ("beta_pr", C.c_int), ("max_batch", C.c_int), ("hbm_budget", C.c_size_t),
                 ("spin_limit", C.c_int64), ("chunk", C.c_int), ("stream", C.c_void_p), ("method", C.c_int),
-                ("smoother", C.c_int)]
+                ("smoother", C.c_int), ("coarse", C.c_int)]
 
 
 _lib = None
@@ -105,6 +107,15 @@ def load_library(path: str = LIB_PATH):
     lib.pod2g_solve_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, I, C.POINTER(Opts), P, P, D, I,
                                         P, IP, DP, IP, P]
     lib.pod2g_solve_noalloc.restype = C.c_int
+    lib.pod2g_surrogate_create.argtypes = [C.c_int64, I, I, I, DP, DP, DP, DP, DP, DP, DP, DP, DP, P,
+                                           C.POINTER(C.c_void_p)]
+    lib.pod2g_surrogate_create.restype = C.c_int
+    lib.pod2g_surrogate_predict_dev.argtypes = [P, I, DP, DP, P]
+    lib.pod2g_surrogate_predict_dev.restype = C.c_int
+    lib.pod2g_surrogate_destroy.argtypes = [P]
+    lib.pod2g_surrogate_destroy.restype = None
+    lib.pod2g_coarse_factor.argtypes = [P, I, DP]
+    lib.pod2g_coarse_factor.restype = C.c_int
     lib.pod2g_destroy.argtypes = [P]
     lib.pod2g_destroy.restype = None
     lib.pod2g_strerror.argtypes = [I]
@@ -146,7 +157,7 @@ class Solver:
 
     def __init__(self, row_ptr, col_idx, bs, phi, *, precision=MIXED_FP32PHI, omega=2.0 / 3.0, pre=1, post=1,
                  beta_pr=False, max_batch=1, hbm_budget=0, chunk=8, spin_limit=0, stream=None, method=0,
-                 elements=None, smoother=0):
+                 elements=None, smoother=0, coarse=None):
         """elements: None (instances are given as assembled block values), or a dict with
         conn [n_el, npe] int, k_ref [(npe*bs)^2] float64 and optional fixed [n_brows] bool:
         the element-factored operator, instances given as element coefficients."""
@@ -170,6 +181,8 @@ class Solver:
         o.stream = C.c_void_p(stream) if stream else None
         o.method = method
         o.smoother = smoother
+        if coarse is not None:
+            o.coarse = coarse
         h = C.c_void_p()
         if elements is None:
             st = lib.pod2g_create(C.byref(pat), phi_cm.ctypes.data_as(C.POINTER(C.c_double)), k, C.byref(o),
@@ -192,6 +205,14 @@ class Solver:
         self.h = h
         self.k, self.bs, self.max_batch, self.precision = k, bs, max_batch, precision
         self.nnzb = int(self.row_ptr[-1])
+
+    def coarse_factor(self, slot):
+        """The slot's k x k lower Cholesky factor L of K_c = Phi^T K Phi (K_c = L L^T)."""
+        L = np.zeros((self.k, self.k))
+        st = self._lib.pod2g_coarse_factor(self.h, slot, L.ctypes.data_as(C.POINTER(C.c_double)))
+        if st != OK:
+            raise Pod2gError(st, "pod2g_coarse_factor")
+        return L
 
     def close(self):
         if getattr(self, "h", None):
@@ -479,3 +500,46 @@ class ServingMix:
             s.serve_stop()
             s.close()
         self.solvers = {}
+
+
+class Surrogate:
+    """Surrogate initial guess on the device (Section 3.2): u = s * Psi (z_mean + z_std * FFNN(theta)).
+
+    weights: an object with psi [n, ks], w1 [H, m], b1 [H], w2 [H, H], b2 [H], w3 [ks, H], b3 [ks],
+    z_mean [ks], z_std [ks] (float64 arrays)."""
+
+    def __init__(self, weights, stream=None):
+        lib = load_library()
+        self._lib = lib
+        psi = np.asfortranarray(np.asarray(weights.psi, dtype=np.float64))
+        self.n, self.ks = psi.shape
+        w1 = np.ascontiguousarray(weights.w1, dtype=np.float64)
+        self.H, self.m = w1.shape
+        arrs = [psi, w1] + [np.ascontiguousarray(getattr(weights, k), dtype=np.float64)
+                            for k in ("b1", "w2", "b2", "w3", "b3", "z_mean", "z_std")]
+        self._keep = arrs
+        h = C.c_void_p()
+        st = lib.pod2g_surrogate_create(self.n, self.m, self.ks, self.H, *[_dptr(a) for a in arrs],
+                                        C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != OK:
+            raise Pod2gError(st, "pod2g_surrogate_create")
+        self.h = h
+
+    def predict_dev(self, theta, scale, x_dev) -> int:
+        """x_dev[q] = prediction for theta[q] (host [nq, m]) and load factor scale[q] (host [nq])."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, self.m)
+        scale = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
+        return self._lib.pod2g_surrogate_predict_dev(self.h, theta.shape[0], _dptr(theta),
+                                                     _dptr(scale) if scale is not None else None,
+                                                     C.c_void_p(x_dev.data_ptr()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.pod2g_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

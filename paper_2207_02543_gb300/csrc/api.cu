@@ -79,6 +79,7 @@ void pod2g_default_opts(pod2g_opts* o) {
     o->chunk = 8;
     o->stream = nullptr;
     o->method = POD2G_PCG;
+    o->coarse = POD2G_COARSE_TENSOR;
 }
 
 const char* pod2g_strerror(int s) {
@@ -218,6 +219,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     if (o.method != POD2G_PCG && o.method != POD2G_STATIONARY) return POD2G_INVALID_ARG;
     if (o.smoother != POD2G_SMOOTHER_JACOBI && o.smoother != POD2G_SMOOTHER_SGS) return POD2G_INVALID_ARG;
     if (o.smoother == POD2G_SMOOTHER_SGS && o.precision != POD2G_FP64 && o.beta_pr) return POD2G_INVALID_ARG;
+    if (o.coarse != POD2G_COARSE_DF && o.coarse != POD2G_COARSE_TENSOR) return POD2G_INVALID_ARG;
     if (o.chunk <= 0) o.chunk = 8;
     // pattern checks: monotone row_ptr, columns in range and sorted, diagonal present
     const int nb = pat->n_brows;
@@ -258,6 +260,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     c->chunk = o.chunk;
     c->method = o.method;
     c->smoother = o.smoother;
+    c->coarse_tc = o.precision != POD2G_FP64 && o.coarse == POD2G_COARSE_TENSOR;
     std::vector<int32_t> h_cnodes;
     std::vector<uint8_t> h_colour;
     if (c->smoother == POD2G_SMOOTHER_SGS) {
@@ -373,6 +376,11 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
         std::memset(c->h_sc2, 0, sizeof(SlotScalars) * Bp);
         *c->h_err2 = 0;
         if (batched_alloc(c) != POD2G_OK) { free_all(c); delete c; return POD2G_INVALID_ARG; }
+        if (c->coarse_tc && c->k > 0 && setup_tc_attributes(c) != POD2G_OK) {
+            free_all(c);
+            delete c;
+            return POD2G_CUDA_ERROR;
+        }
     }
     c->setup_ok.assign(c->B, 0);
     // uploads (synchronous, once)
@@ -459,6 +467,16 @@ int64_t pod2g_launch_count(pod2g_t c) { return c ? (int64_t)c->launches : 0; }
 
 int64_t pod2g_device_bytes(pod2g_t c) { return c ? (int64_t)c->allocated : 0; }
 
+int pod2g_coarse_factor(pod2g_t c, int slot, double* L) {
+    if (!c || !L || slot < 0 || slot >= c->B) return POD2G_INVALID_ARG;
+    if (!c->setup_ok[slot]) return POD2G_INVALID_ARG;
+    if (c->k == 0) return POD2G_OK;
+    P2G_CUDA(cudaMemcpyAsync(L, c->d_Lc + (size_t)slot * c->k * c->k, sizeof(double) * c->k * c->k,
+                             cudaMemcpyDeviceToHost, c->stream));
+    P2G_CUDA(cudaStreamSynchronize(c->stream));
+    return POD2G_OK;
+}
+
 int pod2g_kernel_timing(pod2g_t c, int on) {
     if (!c || c->serving) return POD2G_INVALID_ARG;
     return batched_set_timing(c, on);
@@ -473,6 +491,7 @@ int pod2g_get_tuning(pod2g_t c, pod2g_tuning* out) {
     out->grid_prol = c->grid_prol;
     out->grid_vec = c->grid_vec;
     out->grid_spmv = c->grid_spmv;
+    out->rows_kernel = c->rows_kernel;
     return POD2G_OK;
 }
 
@@ -653,7 +672,9 @@ int pod2g_solve_batch_dev(pod2g_t c, int nslots, const int* slots, const double*
         std::vector<int> maxits(nslots, maxit);
         P2G_TRY(batched_load(c, nslots, slots, b_dev, x0_dev, tols.data(), maxits.data()));
         std::vector<int> lanes(slots, slots + nslots);
-        P2G_TRY(batched_run(c, lanes));
+        const int rr = batched_run(c, lanes);
+        if (rr == POD2G_TIMEOUT) P2G_TRY(batched_retire(c, lanes, POD2G_TIMEOUT));
+        else P2G_TRY(rr);
         P2G_TRY(batched_finalize(c, nslots, slots, x_dev, iters, relres, st.data()));
     }
     int first = POD2G_OK;

@@ -40,6 +40,8 @@
 
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include <chrono>
 #include <cstring>
 #include <cmath>
@@ -599,7 +601,9 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
 #pragma unroll
             for (int a = 0; a < BS; ++a) acc[a] = 0.f;
             if (PRE) {
-                float yj[UNROLL][BS], v[UNROLL][BS * BS];
+                // gathered r.hi and D^-1 (or the stored y1) stay as loaded until the block is used,
+                // so that all loads of the group are in flight together
+                float yj[UNROLL][BS], dj[UNROLL][BS], v[UNROLL][BS * BS];
                 uint64_t dsc[UNROLL];
                 float ce[MF ? POD2G_ELEM_RE : 1];
                 if constexpr (MF) elem_row_coefs(E, i, lane, D.Bp, ce);
@@ -617,15 +621,23 @@ k_smooth1(Dims D, int want, int PRE, const int32_t* __restrict__ row_ptr, const 
 #pragma unroll
                         for (int cc = 0; cc < BS; ++cc) {
                             const long long o = ((long long)j * BS + cc) * D.Bp + lane;
-                            yj[u][cc] = PRE == 2 ? y1[o] : w * dinv[o] * r[o].x;
+                            if (PRE == 2) {
+                                yj[u][cc] = y1[o];
+                            } else {
+                                yj[u][cc] = r[o].x;
+                                dj[u][cc] = dinv[o];
+                            }
                         }
                     },
                     [&](int u) {
                         if constexpr (MF) elem_block_values<BS>(dsc[u], ce, s_kref, v[u]);
+                        float y[BS];
+#pragma unroll
+                        for (int cc = 0; cc < BS; ++cc) y[cc] = PRE == 2 ? yj[u][cc] : w * dj[u][cc] * yj[u][cc];
 #pragma unroll
                         for (int a = 0; a < BS; ++a)
 #pragma unroll
-                            for (int cc = 0; cc < BS; ++cc) acc[a] = __fmaf_rn(v[u][a * BS + cc], yj[u][cc], acc[a]);
+                            for (int cc = 0; cc < BS; ++cc) acc[a] = __fmaf_rn(v[u][a * BS + cc], y[cc], acc[a]);
                     });
             }
 #pragma unroll
@@ -1123,6 +1135,368 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
     if (threadIdx.x == 0) *counter = 0u;
 }
 
+// ---------------------------------------------------------------------------- warp-staged row kernels
+// The outer SpMV, the pre-smoothing pass and the post-smoothing pass of assembled
+// operators with 4 <= Bp <= 64 slot lanes and damped-Jacobi relaxation, restructured
+// so that no thread waits on the value stream (the bulk of their bytes):
+//   * a warp owns RPW = 32 / LR consecutive block rows (a "row group"; LR = Bp / SPT
+//     lanes per row, SPT slots per lane, so that a lane reads SPT consecutive slots
+//     with one vector access) and walks its groups in grid-stride order, so that the
+//     rows in flight across the GPU form one front and gathered entries are reused
+//     from L2;
+//   * a group is processed in chunks of WS_U blocks per row. The values of a row's
+//     chunk are contiguous ([block][bs*bs][Bp]); one lane per row copies them with
+//     cp.async.bulk into the warp's ring of WS_STAGES shared-memory buffers (one
+//     mbarrier each), two chunks ahead of the one being used;
+//   * the gathered vector entries of the next chunk are loaded into registers before
+//     the current chunk is used, with column indices loaded one chunk earlier still.
+// Arithmetic and per-slot reduction order are fixed per slot (a lane always owns the
+// same slots), so a result does not depend on the other slots. A bounded mbarrier
+// wait that expires sets *err to 2, waits (bounded) for the copies the warp still has
+// in flight and skips the warp's remaining rows; every CTA still joins the reductions.
+#define WS_STAGES 3
+template <int BS> struct WsU { static constexpr int U = BS == 1 ? 9 : 3; };
+
+// floats per row slot of a stage buffer: the chunk's values, padded so that the RPW
+// rows of a warp read disjoint banks (row stride / LR odd)
+__host__ __device__ constexpr int ws_row_stride(int bs, int Bp, int spt) {
+    return (32 / (Bp / spt) > 1 && ((bs == 1 ? 9 : 3) * bs * bs) % 2 == 0) ? (bs == 1 ? 9 : 3) * bs * bs * Bp + Bp / spt
+                                                                          : (bs == 1 ? 9 : 3) * bs * bs * Bp;
+}
+
+template <int SPT>
+__device__ __forceinline__ void ws_ld2(const float2* p, float2 (&o)[SPT]) {
+    if constexpr (SPT == 1) {
+        o[0] = *p;
+    } else if constexpr (SPT == 2) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = make_float2(v.x, v.y); o[1] = make_float2(v.z, v.w);
+    } else {
+        static_assert(SPT <= 2, "one or two slots per lane");
+    }
+}
+template <int SPT>
+__device__ __forceinline__ void ws_ld1(const float* p, float (&o)[SPT]) {
+    if constexpr (SPT == 1) {
+        o[0] = *p;
+    } else if constexpr (SPT == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        o[0] = v.x; o[1] = v.y;
+    } else {
+        static_assert(SPT <= 2, "one or two slots per lane");
+    }
+}
+
+// Position of a warp in its walk: row group g (chunk c of nch), and the block range of
+// the lane's row in that group.
+struct WsCur {
+    int g, c, nch, beg, len;
+};
+
+// KIND 0: q = K p (double-float), partial p^T q, last cluster alpha (as k_spmv).
+// KIND 1: r1 = r - K (omega D^-1 r), partial ||r||^2 (as k_smooth1 with PRE = 1).
+// KIND 2: s = y2 + omega D^-1 (r - K y2), partial r^T s (and r^T s_old), last cluster
+//         beta (as k_post with POST = 1).
+template <int BS, int SPT, int KIND>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, 2)
+k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+          const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ vin,
+          const float* __restrict__ yin, float2* __restrict__ qout, float* __restrict__ out, double* part,
+          unsigned* counter, SlotScalars* sc, int* err) {
+    constexpr int U = WsU<BS>::U;
+    constexpr int BB = BS * BS;
+    extern __shared__ __align__(16) float s_ws[];
+    __shared__ double s_tmp[POD2G_THREADS * SPT];
+    __shared__ double s_out[2 * POD2G_MAX_BP];
+    const int Bp = D.Bp;
+    const int LR = Bp / SPT, RPW = 32 / LR;
+    const int RS = ws_row_stride(BS, Bp, SPT);
+    const int SF = RPW * RS;  // floats per stage buffer
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = lane / LR, slot0 = (lane % LR) * SPT;
+    const int NG = (D.nb + RPW - 1) / RPW;
+    const int TW = gridDim.x * (POD2G_THREADS / 32);
+    float* ring = s_ws + (size_t)warp * WS_STAGES * SF;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_ws + (size_t)(POD2G_THREADS / 32) * WS_STAGES * SF) +
+                     warp * WS_STAGES;
+    bool on[SPT];
+    bool any_on = false, all_on = true;
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) {
+        on[s] = sc[slot0 + s].state == want;
+        any_on |= on[s];
+        all_on &= on[s];
+    }
+    const bool work = __any_sync(0xffffffffu, any_on);  // uniform over the grid (all warps see all slots)
+    if (lane == 0) {
+        for (int st = 0; st < WS_STAGES; ++st) mbar_init(bars + st, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    const float w = (float)D.omega;
+    // per-slot partial sums (double-float pairs accumulated in FP32)
+    float d1h[SPT], d1l[SPT], d2h[SPT], d2l[SPT];
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) { d1h[s] = 0.f; d1l[s] = 0.f; d2h[s] = 0.f; d2l[s] = 0.f; }
+
+    auto load_group = [&](WsCur& q) {
+        const int i = q.g * RPW + r;
+        q.beg = 0;
+        q.len = 0;
+        if (q.g < NG && i < D.nb) {
+            q.beg = __ldg(row_ptr + i);
+            q.len = __ldg(row_ptr + i + 1) - q.beg;
+        }
+        const unsigned mx = __reduce_max_sync(0xffffffffu, (unsigned)q.len);
+        q.nch = (int)((mx + U - 1) / U);
+    };
+    auto next = [&](WsCur q) {
+        if (q.g >= NG) return q;
+        if (++q.c >= q.nch) {
+            q.g += TW;
+            q.c = 0;
+            load_group(q);
+        }
+        return q;
+    };
+    auto nblk = [&](const WsCur& q) { return q.g < NG ? min(U, max(0, q.len - q.c * U)) : 0; };
+    // copies of the chunk of state q into stage buffer st (all lanes call)
+    auto issue = [&](const WsCur& q, int st) {
+        if (q.g >= NG) return;
+        const int nbk = nblk(q);
+        const unsigned bytes = (unsigned)nbk * BB * Bp * 4u;
+        const unsigned total = __reduce_add_sync(0xffffffffu, (lane % LR) == 0 ? bytes : 0u);
+        if (lane == 0) mbar_expect_tx(bars + st, total);
+        __syncwarp();
+        if ((lane % LR) == 0 && nbk > 0)
+            bulk_load(ring + (size_t)st * SF + r * RS, vals + ((long long)q.beg + q.c * U) * BB * Bp, bytes, bars + st);
+    };
+    auto load_cols = [&](const WsCur& q, int (&cj)[U]) {
+        const int nbk = nblk(q);
+#pragma unroll
+        for (int u = 0; u < U; ++u) cj[u] = u < nbk ? __ldg(col_idx + q.beg + q.c * U + u) : -1;
+    };
+    // gathered entries of the chunk, held as loaded until the chunk is used (so that no thread
+    // waits on them a chunk early): KIND 0 p (double-float); KIND 1 (r.hi, D^-1); KIND 2 y
+    using GT = typename std::conditional<KIND == 2, float, float2>::type;
+    auto gather = [&](const int (&cj)[U], GT (&G)[U][BS][SPT]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (cj[u] < 0) continue;
+#pragma unroll
+            for (int cc = 0; cc < BS; ++cc) {
+                const long long o = ((long long)cj[u] * BS + cc) * Bp + slot0;
+                if constexpr (KIND == 0) {
+                    ws_ld2<SPT>(vin + o, G[u][cc]);
+                } else if constexpr (KIND == 1) {
+                    float2 rv[SPT];
+                    float dv[SPT];
+                    ws_ld2<SPT>(vin + o, rv);
+                    ws_ld1<SPT>(dinv + o, dv);
+#pragma unroll
+                    for (int s = 0; s < SPT; ++s) G[u][cc][s] = make_float2(rv[s].x, dv[s]);
+                } else {
+                    ws_ld1<SPT>(yin + o, G[u][cc]);
+                }
+            }
+        }
+    };
+
+    WsCur C{blockIdx.x * (POD2G_THREADS / 32) + warp, 0, 0, 0, 0};
+    if (!work) C.g = NG;
+    load_group(C);
+    int t = 0, issued = 0;
+    issue(C, 0);
+    issued = C.g < NG ? 1 : 0;
+    WsCur Gs = next(C);
+    issue(Gs, 1);
+    issued += Gs.g < NG ? 1 : 0;
+    WsCur P = next(Gs);
+    int cj[U], cjn[U];
+    GT G[U][BS][SPT], Gn[U][BS][SPT];
+    load_cols(C, cj);
+    gather(cj, G);
+    load_cols(Gs, cjn);
+    // accumulators of the lane's row and its own-row operands (loaded at the group's first chunk)
+    float ah[BS][SPT], al[BS][SPT];
+    float2 own2[BS][SPT];      // KIND 0: p; KIND 1, 2: r
+    float owny[BS][SPT], ownd[BS][SPT], owns[BS][SPT];
+    bool bad = false;
+    while (C.g < NG) {
+        // 1. gathers of the next chunk
+        gather(cjn, Gn);
+        // 2. copies two chunks ahead, and their column indices
+        issue(P, (t + 2) % WS_STAGES);
+        issued += P.g < NG ? 1 : 0;
+        int cjp[U];
+        load_cols(P, cjp);
+        // 3. this chunk
+        if (C.c == 0) {
+#pragma unroll
+            for (int a = 0; a < BS; ++a)
+#pragma unroll
+                for (int s = 0; s < SPT; ++s) { ah[a][s] = 0.f; al[a][s] = 0.f; }
+            const int i = C.g * RPW + r;
+            if (i < D.nb) {
+#pragma unroll
+                for (int a = 0; a < BS; ++a) {
+                    const long long o = ((long long)i * BS + a) * Bp + slot0;
+                    ws_ld2<SPT>(vin + o, own2[a]);
+                    if constexpr (KIND == 2) {
+                        ws_ld1<SPT>(yin + o, owny[a]);
+                        ws_ld1<SPT>(dinv + o, ownd[a]);
+                        if (pr) ws_ld1<SPT>(out + o, owns[a]);
+                    }
+                }
+            }
+        }
+        const int st = t % WS_STAGES;
+        bad = __any_sync(0xffffffffu, !mbar_wait(bars + st, (unsigned)(t / WS_STAGES) & 1u, MBAR_POLLS));
+        if (bad) break;
+        const float* vb = ring + (size_t)st * SF + r * RS + slot0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (cj[u] < 0) continue;
+#pragma unroll
+            for (int a = 0; a < BS; ++a)
+#pragma unroll
+                for (int cc = 0; cc < BS; ++cc) {
+                    float v[SPT];
+                    ws_ld1<SPT>(vb + (u * BB + a * BS + cc) * Bp, v);
+#pragma unroll
+                    for (int s = 0; s < SPT; ++s) {
+                        if constexpr (KIND == 0) df_acc_fma(ah[a][s], al[a][s], v[s], G[u][cc][s].x, G[u][cc][s].y);
+                        else if constexpr (KIND == 1)
+                            ah[a][s] = __fmaf_rn(v[s], w * G[u][cc][s].y * G[u][cc][s].x, ah[a][s]);
+                        else ah[a][s] = __fmaf_rn(v[s], G[u][cc][s], ah[a][s]);
+                    }
+                }
+        }
+        if (C.c == C.nch - 1) {
+            const int i = C.g * RPW + r;
+            if (i < D.nb && any_on) {
+#pragma unroll
+                for (int a = 0; a < BS; ++a) {
+                    const long long o = ((long long)i * BS + a) * Bp + slot0;
+                    if constexpr (KIND == 0) {
+                        float2 qv[SPT];
+#pragma unroll
+                        for (int s = 0; s < SPT; ++s) {
+                            qv[s] = df_norm(ah[a][s], al[a][s]);
+                            if (on[s]) {
+                                const float2 pv = own2[a][s];
+                                df_acc_fma(d1h[s], d1l[s], pv.x, qv[s].x, qv[s].y);
+                                d1l[s] = __fmaf_rn(pv.y, qv[s].x, d1l[s]);
+                            }
+                        }
+                        if (SPT == 2 && all_on) {
+                            *reinterpret_cast<float4*>(qout + o) = make_float4(qv[0].x, qv[0].y, qv[1].x, qv[1].y);
+                        } else {
+#pragma unroll
+                            for (int s = 0; s < SPT; ++s)
+                                if (on[s]) qout[o + s] = qv[s];
+                        }
+                    } else if constexpr (KIND == 1) {
+#pragma unroll
+                        for (int s = 0; s < SPT; ++s) {
+                            if (!on[s]) continue;
+                            const float rv = own2[a][s].x;
+                            out[o + s] = rv - ah[a][s];
+                            d1h[s] = __fmaf_rn(rv, rv, d1h[s]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < SPT; ++s) {
+                            if (!on[s]) continue;
+                            const float2 rv = own2[a][s];
+                            const float sv = __fmaf_rn(w * ownd[a][s], rv.x - ah[a][s], owny[a][s]);
+                            if (pr) df_acc_fma(d2h[s], d2l[s], owns[a][s], rv.x, rv.y);
+                            out[o + s] = sv;
+                            df_acc_fma(d1h[s], d1l[s], sv, rv.x, rv.y);
+                        }
+                    }
+                }
+            }
+        }
+        // 4. advance
+        __syncwarp();  // every lane is done with buffer st before it is refilled
+        C = Gs;
+        Gs = P;
+        P = next(P);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cj[u] = cjn[u];
+            cjn[u] = cjp[u];
+#pragma unroll
+            for (int cc = 0; cc < BS; ++cc)
+#pragma unroll
+                for (int s = 0; s < SPT; ++s) G[u][cc][s] = Gn[u][cc][s];
+        }
+        ++t;
+    }
+    if (bad) {
+        // a copy did not complete in time: report, let the copies in flight land, skip the rest
+        if (lane == 0) {
+            atomicExch(err, 2);
+            for (int k = t; k < issued; ++k)
+                mbar_wait(bars + k % WS_STAGES, (unsigned)(k / WS_STAGES) & 1u, MBAR_POLLS);
+        }
+        __syncwarp();
+    }
+    // per-slot CTA sums (entry tid*SPT + s belongs to slot (tid*SPT + s) mod Bp)
+    auto cta_sum = [&](const float* h, const float* l, double* dst) {
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) s_tmp[threadIdx.x * SPT + s] = (double)h[s] + (double)l[s];
+        __syncthreads();
+        if ((int)threadIdx.x < Bp) {
+            double acc = 0.0;
+            for (int e = threadIdx.x; e < POD2G_THREADS * SPT; e += Bp) acc += s_tmp[e];
+            dst[threadIdx.x] = acc;
+        }
+        __syncthreads();
+    };
+    cta_sum(d1h, d1l, s_out);
+    if constexpr (KIND == 2) cta_sum(d2h, d2l, s_out + Bp);
+    cluster_store(s_out, KIND == 2 ? 2 * Bp : Bp, part + (long long)(blockIdx.x / CLUSTER) * Bp * 2);
+    if constexpr (KIND == 1) return;
+    if (!last_cluster_arrive(counter, KIND == 0 ? D.NPs : D.NP)) return;
+    if constexpr (KIND == 0) {
+        const double pq = grid_lane_total(part, D.NPs, 2 * Bp, Bp, s_tmp);
+        if ((int)threadIdx.x < Bp) {
+            SlotScalars& S = sc[threadIdx.x];
+            if (S.state == want) {
+                if (S.iters >= S.maxit) {
+                    S.state = SLOT_DONE; S.result = POD2G_NOT_CONVERGED; S.alpha = 0.0;
+                } else if (!(pq > 0.0) || !isfinite(pq)) {
+                    S.state = SLOT_DONE; S.result = isfinite(pq) ? POD2G_BREAKDOWN : POD2G_NONFINITE; S.alpha = 0.0;
+                } else {
+                    S.alpha = D.stat ? 1.0 : S.rs / pq;
+                    S.iters += 1;
+                }
+            }
+        }
+    } else {
+        const double rs = grid_lane_total(part, D.NP, 2 * Bp, Bp, s_tmp);
+        const double rsx = pr ? grid_lane_total(part + Bp, D.NP, 2 * Bp, Bp, s_tmp) : 0.0;
+        if ((int)threadIdx.x < Bp) {
+            SlotScalars& S = sc[threadIdx.x];
+            if (S.state == want) {
+                if (!(rs > 0.0) || !isfinite(rs)) {
+                    S.state = SLOT_DONE;
+                    S.result = isfinite(rs) ? POD2G_BREAKDOWN : POD2G_NONFINITE;
+                } else {
+                    S.beta = (S.first || D.stat) ? 0.0 : (pr ? (rs - rsx) / S.rs : rs / S.rs);
+                    S.rs = rs;
+                    S.first = 0;
+                    if (want == SLOT_JOINING) S.state = SLOT_ACTIVE;
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------- host side
@@ -1300,6 +1674,71 @@ static void launch_post(pod2g_ctx* c, Dims D, int want) {
                                                   c->d_counters + CNT_POST, c->d_sc);
 }
 
+// ---- warp-staged row kernels (k_rows_ws): applicability, shared memory, launch
+static int ws_spt(int Bp) { return Bp > 32 ? Bp / 32 : 1; }
+// the staged kernels apply to assembled operators with 4 <= Bp <= 64 and Jacobi relaxation
+static bool ws_applies(const pod2g_ctx* c) {
+    return !c->elem && c->precision != POD2G_FP64 && c->Bp >= 4 && c->Bp <= 64 &&
+           c->smoother == POD2G_SMOOTHER_JACOBI;
+}
+static size_t ws_smem(int bs, int Bp) {
+    const int spt = ws_spt(Bp), rpw = 32 / (Bp / spt);
+    return (size_t)(POD2G_THREADS / 32) * WS_STAGES * ((size_t)rpw * ws_row_stride(bs, Bp, spt) * 4 + 8);
+}
+static bool ws_spmv(const pod2g_ctx* c) { return ws_applies(c) && (c->rows_kernel & 2); }
+static bool ws_smooth(const pod2g_ctx* c) { return ws_applies(c) && (c->rows_kernel & 1); }
+
+#define WS_DISPATCH(KIND, ...)                                                            \
+    do {                                                                                   \
+        const bool two_ = ws_spt(c->Bp) == 2;                                              \
+        if (c->bs == 1) {                                                                  \
+            if (two_) k_rows_ws<1, 2, KIND> __VA_ARGS__;                                   \
+            else k_rows_ws<1, 1, KIND> __VA_ARGS__;                                        \
+        } else if (c->bs == 2) {                                                           \
+            if (two_) k_rows_ws<2, 2, KIND> __VA_ARGS__;                                   \
+            else k_rows_ws<2, 1, KIND> __VA_ARGS__;                                        \
+        } else {                                                                           \
+            if (two_) k_rows_ws<3, 2, KIND> __VA_ARGS__;                                   \
+            else k_rows_ws<3, 1, KIND> __VA_ARGS__;                                        \
+        }                                                                                  \
+    } while (0)
+
+static void launch_spmv_ws(pod2g_ctx* c, Dims D, int want) {
+    const size_t sm = ws_smem(c->bs, c->Bp);
+    WS_DISPATCH(0, <<<c->grid_spmv, POD2G_THREADS, sm, c->stream>>>(
+                       D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_pdf, nullptr,
+                       c->d_qdf, nullptr, c->d_part, c->d_counters + CNT_SPMV, c->d_sc, c->d_err));
+}
+static void launch_smooth1_ws(pod2g_ctx* c, Dims D, int want) {
+    const size_t sm = ws_smem(c->bs, c->Bp);
+    WS_DISPATCH(1, <<<D.G, POD2G_THREADS, sm, c->stream>>>(
+                       D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_rdf, nullptr,
+                       nullptr, c->d_y32, c->d_part, nullptr, c->d_sc, c->d_err));
+}
+static void launch_post_ws(pod2g_ctx* c, Dims D, int want) {
+    const size_t sm = ws_smem(c->bs, c->Bp);
+    WS_DISPATCH(2, <<<D.G, POD2G_THREADS, sm, c->stream>>>(
+                       D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_rdf,
+                       c->d_y32, nullptr, c->d_s32, c->d_part, c->d_counters + CNT_POST, c->d_sc, c->d_err));
+}
+static int ws_set_attributes(pod2g_ctx* c) {
+    const int sm = (int)ws_smem(c->bs, c->Bp);
+    const void* fns[3] = {nullptr, nullptr, nullptr};
+#define WS_FN(BS_, SPT_)                                                   \
+    if (c->bs == BS_ && ws_spt(c->Bp) == SPT_) {                           \
+        fns[0] = (const void*)k_rows_ws<BS_, SPT_, 0>;                     \
+        fns[1] = (const void*)k_rows_ws<BS_, SPT_, 1>;                     \
+        fns[2] = (const void*)k_rows_ws<BS_, SPT_, 2>;                     \
+    }
+    WS_FN(1, 1) WS_FN(1, 2) WS_FN(2, 1) WS_FN(2, 2) WS_FN(3, 1) WS_FN(3, 2)
+#undef WS_FN
+    for (const void* f : fns) {
+        if (!f) return POD2G_INVALID_ARG;
+        P2G_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    }
+    return POD2G_OK;
+}
+
 // Event-record node after a kernel of a captured iteration (timing mode only).
 static int mark(pod2g_ctx* c) {
     P2G_TRY(pod2g_check_launch(c));
@@ -1317,7 +1756,8 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
     int st = POD2G_OK;
     if (gs && c->pre) LAUNCH_BS(st = launch_gs, (c, D, want, 0));   // y1: forward sweep from zero, into s
     P2G_TRY(st);
-    LAUNCH_BS(launch_smooth1, (c, D, want));
+    if (ws_smooth(c) && c->pre == 1) launch_smooth1_ws(c, D, want);
+    else LAUNCH_BS(launch_smooth1, (c, D, want));
     P2G_TRY(mark(c));
     if (c->kp > 0) launch_restrict(c, D, want);
     P2G_TRY(mark(c));
@@ -1327,7 +1767,8 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
     P2G_TRY(mark(c));
     if (gs && c->post) LAUNCH_BS(st = launch_gs, (c, D, want, 1));  // backward sweep on s in place
     P2G_TRY(st);
-    LAUNCH_BS(launch_post, (c, D, want));
+    if (ws_smooth(c) && c->post == 1) launch_post_ws(c, D, want);
+    else LAUNCH_BS(launch_post, (c, D, want));
     P2G_TRY(mark(c));
     return POD2G_OK;
 }
@@ -1340,9 +1781,12 @@ static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     k_p<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_s32, c->d_pdf, c->d_sc, total);
     P2G_TRY(mark(c));
     const ElemOp E = elem_op(c);
-    LAUNCH_BS(k_spmv, <<<c->grid_spmv, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx, c->d_vals32,
-                                                             E, c->d_pdf, c->d_qdf, c->d_part,
-                                                             c->d_counters + CNT_SPMV, c->d_sc));
+    if (ws_spmv(c))
+        launch_spmv_ws(c, D, SLOT_ACTIVE);
+    else
+        LAUNCH_BS(k_spmv, <<<c->grid_spmv, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx,
+                                                                 c->d_vals32, E, c->d_pdf, c->d_qdf, c->d_part,
+                                                                 c->d_counters + CNT_SPMV, c->d_sc));
     P2G_TRY(mark(c));
     k_upd<<<ge, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_xdf, c->d_rdf, c->d_pdf, c->d_qdf, c->d_sc, total);
     P2G_TRY(mark(c));
@@ -1359,6 +1803,27 @@ int batched_alloc(pod2g_ctx* c) {
     c->grid_restrict = batched_grid(c->num_sms, (long long)2 * c->num_sms * POD2G_THREADS);
     c->grid_prol = 8 * c->num_sms;
     c->grid_vec = 8 * c->num_sms;
+    c->rows_kernel = 0;
+    if (ws_applies(c)) {
+        // staged row kernels by default: one wave of resident CTAs for the row kernels
+        P2G_TRY(ws_set_attributes(c));
+        int occ = 0;
+        const int sm = (int)ws_smem(c->bs, c->Bp);
+#define WS_OCC(BS_, SPT_)                                                                                   \
+        if (c->bs == BS_ && ws_spt(c->Bp) == SPT_)                                                          \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_ws<BS_, SPT_, 0>, POD2G_THREADS, sm);
+        WS_OCC(1, 1) WS_OCC(1, 2) WS_OCC(2, 1) WS_OCC(2, 2) WS_OCC(3, 1) WS_OCC(3, 2)
+#undef WS_OCC
+        cudaGetLastError();
+        if (occ > 0) {
+            // four waves of resident CTAs (measured faster than one: the hardware keeps every SM
+            // fed as 8-CTA clusters retire)
+            c->rows_kernel = 3;
+            c->ws_occ = occ;
+            c->grid_rows = std::max(CLUSTER, std::min(8 * c->num_sms, 4 * occ * c->num_sms) / CLUSTER * CLUSTER);
+            c->grid_spmv = c->grid_rows;
+        }
+    }
     if (c->precision != POD2G_FP64 && c->kp > 0) {
         const int sm_r = (int)(restrict_bulk_smem(c->Bp, c->kp) ? restrict_bulk_smem(c->Bp, c->kp)
                                                                  : restrict_smem(c->Bp, c->kp));
@@ -1540,6 +2005,22 @@ int batched_run(pod2g_ctx* c, const std::vector<int>& lanes) {
     }
 }
 
+// Lanes that are still iterating when the host gives up (its bounded wait expired) are
+// marked DONE with `result`: later launches skip them and their last iterate can be stored.
+int batched_retire(pod2g_ctx* c, const std::vector<int>& lanes, int result) {
+    P2G_CUDA(cudaStreamSynchronize(c->stream));
+    P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
+    P2G_CUDA(cudaStreamSynchronize(c->stream));
+    for (int b : lanes)
+        if (c->h_sc[b].state != SLOT_DONE) {
+            c->h_sc[b].state = SLOT_DONE;
+            c->h_sc[b].result = result;
+        }
+    P2G_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyHostToDevice, c->stream));
+    P2G_CUDA(cudaStreamSynchronize(c->stream));
+    return POD2G_OK;
+}
+
 // true FP64 residual for the finished lanes, x out, per-slot results
 int batched_finalize(pod2g_ctx* c, int nslots, const int* slots, double* x_dev, int* iters, double* relres,
                      int* status) {
@@ -1576,6 +2057,9 @@ int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
     if (t->grid_spmv < CLUSTER || t->grid_spmv % CLUSTER || t->grid_spmv > 8 * sms) return POD2G_INVALID_ARG;
     if (t->grid_restrict < CLUSTER || t->grid_restrict % CLUSTER || t->grid_restrict > 4 * sms) return POD2G_INVALID_ARG;
     if (t->grid_prol < 1 || t->grid_prol > 8 * sms || t->grid_vec < 1 || t->grid_vec > 8 * sms) return POD2G_INVALID_ARG;
+    if (t->rows_kernel < 0 || t->rows_kernel > 3 || (t->rows_kernel && !(ws_applies(c) && c->ws_occ > 0)))
+        return POD2G_INVALID_ARG;
+    c->rows_kernel = t->rows_kernel;
     c->grid_rows = t->grid_rows;
     c->grid_spmv = t->grid_spmv;
     c->grid_restrict = t->grid_restrict;
@@ -1609,11 +2093,33 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
         cand[j].grid_prol = std::min(vec_f[j] * sms, need_vec);
         cand[j].grid_vec = std::min(vec_f[j] * sms, need_vec);
     }
+    // the warp-staged row kernels (where they apply) with one to eight waves of resident CTAs
+    const bool ws = ws_applies(c) && c->ws_occ > 0;
+    const int wave = c->ws_occ * sms;
+    const int ws_f[NC] = {1, 2, 3, 4, 8};
+    pod2g_tuning cand_ws[NC];
+    for (int j = 0; j < NC; ++j) {
+        cand[j].rows_kernel = 0;
+        cand_ws[j] = cand[j];
+        cand_ws[j].rows_kernel = 3;
+        cand_ws[j].grid_rows = r8(ws_f[j] * wave, 8 * sms);
+        cand_ws[j].grid_spmv = cand_ws[j].grid_rows;
+    }
     const bool timing0 = c->timing;
     std::vector<double> tol(nslots, 0.0);
     std::vector<int> maxit(nslots, iters + 16 * c->chunk);
     std::vector<int> lanes(slots, slots + nslots);
-    double t_rows[NC], t_spmv[NC], t_res[NC], t_prol[NC], t_vec[NC];
+    double t_rows[2 * NC], t_spmv[2 * NC], t_res[NC], t_prol[NC], t_vec[NC];
+    for (int j = 0; j < 2 * NC; ++j) t_rows[j] = t_spmv[j] = 1e300;
+    for (int j = 0; j < NC && ws; ++j) {
+        P2G_TRY(batched_set_tuning(c, &cand_ws[j]));
+        P2G_TRY(batched_set_timing(c, 1));
+        P2G_TRY(batched_load(c, nslots, slots, b_dev, nullptr, tol.data(), maxit.data()));
+        for (int it = 0; it < iters; it += c->chunk) P2G_TRY(batched_chunk(c));
+        auto per = [&](int k) { return c->kt_n[k] ? c->kt_ms[k] / (double)c->kt_n[k] : 0.0; };
+        t_spmv[NC + j] = per(1);
+        t_rows[NC + j] = per(3) + per(7);
+    }
     for (int j = 0; j < NC; ++j) {
         P2G_TRY(batched_set_tuning(c, &cand[j]));
         P2G_TRY(batched_set_timing(c, 1));
@@ -1626,18 +2132,21 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
         t_res[j] = per(4);                        // k_restrict
         t_prol[j] = per(6);                       // k_prol
     }
-    auto best = [&](const double* t) {
+    auto best = [&](const double* t, int m) {
         int b = 0;
-        for (int j = 1; j < NC; ++j)
+        for (int j = 1; j < m; ++j)
             if (t[j] < t[b]) b = j;
         return b;
     };
+    auto row_cand = [&](int j) -> const pod2g_tuning& { return j < NC ? cand[j] : cand_ws[j - NC]; };
     pod2g_tuning pick;
-    pick.grid_rows = cand[best(t_rows)].grid_rows;
-    pick.grid_spmv = cand[best(t_spmv)].grid_spmv;
-    pick.grid_restrict = cand[best(t_res)].grid_restrict;
-    pick.grid_prol = cand[best(t_prol)].grid_prol;
-    pick.grid_vec = cand[best(t_vec)].grid_vec;
+    const int br = best(t_rows, 2 * NC), bsp = best(t_spmv, 2 * NC);
+    pick.grid_rows = row_cand(br).grid_rows;
+    pick.grid_spmv = row_cand(bsp).grid_spmv;
+    pick.rows_kernel = (br >= NC ? 1 : 0) | (bsp >= NC ? 2 : 0);
+    pick.grid_restrict = cand[best(t_res, NC)].grid_restrict;
+    pick.grid_prol = cand[best(t_prol, NC)].grid_prol;
+    pick.grid_vec = cand[best(t_vec, NC)].grid_vec;
     P2G_TRY(batched_set_tuning(c, &pick));
     P2G_TRY(batched_set_timing(c, timing0 ? 1 : 0));
     // leave the slots idle

@@ -52,6 +52,7 @@ struct pod2g_ctx {
     int precision = 0, pre = 1, post = 1, beta_pr = 0, B = 1, Bp = 1, chunk = 8;
     int method = 0;                     // POD2G_PCG or POD2G_STATIONARY
     int smoother = 0;                   // POD2G_SMOOTHER_JACOBI or POD2G_SMOOTHER_SGS
+    bool coarse_tc = false;             // K_c = Phi^T (K Phi) contracted on the tensor cores (mixed paths)
     // multicolour order of the Gauss-Seidel smoother
     int ncolours = 0;
     std::vector<int> coff;              // [ncolours + 1] offsets into d_cnodes
@@ -140,6 +141,8 @@ struct pod2g_ctx {
     int grid_restrict = 0;              // CTAs of the restriction (multiple of 8)
     int grid_prol = 0;                  // CTAs of the prolongation
     int grid_vec = 0;                   // CTAs of the vector updates (p, x/r)
+    int rows_kernel = 0;                // bit 0: staged smoother row kernels, bit 1: staged outer SpMV
+    int ws_occ = 0;                     // resident CTAs per SM of the staged row kernels (0: not available)
     cudaGraphExec_t graph_exec = nullptr;
     // per-kernel timing (event-record nodes around each kernel of the captured iterations)
     bool timing = false;
@@ -344,6 +347,7 @@ int setup_values(pod2g_ctx* c, int slot, const double* vals_dev);
 int setup_values_batch(pod2g_ctx* c, int nslots, const int* slots, const double* values_dev);
 int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev);
 int setup_theta(pod2g_ctx* c, int slot, const double* theta_dev);
+int setup_tc_attributes(pod2g_ctx* c);
 // doubles describing one instance: matrix values, or element coefficients
 static inline size_t instance_len(const pod2g_ctx* c) {
     return c->elem ? (size_t)c->n_el : (size_t)c->nnzb * c->bs * c->bs;
@@ -354,6 +358,7 @@ static inline int setup_instance(pod2g_ctx* c, int slot, const double* dev) {
 int batched_load(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, const double* x0_dev,
                  const double* tol, const int* maxit);
 int batched_run(pod2g_ctx* c, const std::vector<int>& lanes);
+int batched_retire(pod2g_ctx* c, const std::vector<int>& lanes, int result);
 int batched_chunk(pod2g_ctx* c);
 int batched_set_timing(pod2g_ctx* c, int on);
 int batched_grid(int num_sms, long long items);

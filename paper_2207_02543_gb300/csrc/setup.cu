@@ -160,6 +160,54 @@ __global__ void k_elem_stage(ElemOp E, const int32_t* __restrict__ row_ptr, int 
     }
 }
 
+// Last CTA of a K_c contraction: sum the nparts partial k x k matrices in part order
+// (deterministic), symmetrise into Lout, and factor it in place (lower triangle) in FP64.
+// A pivot below 64 eps times its original diagonal entry means K_c is numerically singular
+// (e.g. linearly dependent modes) and is reported as not SPD.
+__device__ void ac_reduce_factor(const double* part, int nparts, int k, double* Ac, double* Lout, int* status) {
+    const int npairs = k * k;
+    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < nparts; ++g) s += part[(long long)g * npairs + pr];
+        Ac[pr] = s;
+    }
+    __syncthreads();
+    // symmetrise into L (lower triangle used)
+    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+        int i = pr / k, j = pr - i * k;
+        Lout[pr] = 0.5 * (Ac[i * k + j] + Ac[j * k + i]);
+    }
+    __syncthreads();
+    // right-looking Cholesky in place (lower triangle), FP64
+    __shared__ int fail;
+    __shared__ double diag0[POD2G_MAX_K];
+    if (threadIdx.x == 0) fail = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) diag0[j] = Lout[j * k + j];
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            double d = Lout[j * k + j];
+            if (!(d > 64.0 * 2.220446049250313e-16 * diag0[j]) || !isfinite(d)) { fail = 1; d = 1.0; }
+            Lout[j * k + j] = sqrt(d);
+        }
+        __syncthreads();
+        double ljj = Lout[j * k + j];
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) Lout[i * k + j] /= ljj;
+        __syncthreads();
+        int m = k - j - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = j + 1 + e / m, t = j + 1 + e % m;
+            if (t <= i) Lout[i * k + t] -= Lout[i * k + j] * Lout[t * k + j];
+        }
+        __syncthreads();
+    }
+    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+        int i = pr / k, j = pr - i * k;
+        if (j > i) Lout[pr] = 0.0;
+    }
+    if (threadIdx.x == 0 && fail) atomicCAS(status, (int)POD2G_OK, (int)POD2G_NOT_SPD);
+}
+
 #define AC_TILE 32
 
 // Contraction K_c = Phi^T W (k x k), split over CTAs along the n rows; the last
@@ -224,52 +272,198 @@ __global__ void k_ac(const void* __restrict__ phi_v, const void* __restrict__ W_
         part[(long long)blockIdx.x * npairs + pr] = DF ? ((double)acc_hi[q] + (double)acc_lo[q]) : acc[q];
     }
     if (!last_cta_arrive(counter)) return;
-    // ---- last CTA: reduce partials in CTA order
-    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
-        double s = 0.0;
-        for (int g = 0; g < (int)gridDim.x; ++g) s += part[(long long)g * npairs + pr];
-        Ac[pr] = s;
-    }
-    __syncthreads();
-    // symmetrise into L (lower triangle used)
-    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
-        int i = pr / k, j = pr - i * k;
-        Lout[pr] = 0.5 * (Ac[i * k + j] + Ac[j * k + i]);
-    }
-    __syncthreads();
-    // right-looking Cholesky in place (lower triangle), FP64. A pivot below
-    // 64 eps times its original diagonal entry means K_c is numerically singular
-    // (e.g. linearly dependent modes) and is reported as not SPD.
-    __shared__ int fail;
-    __shared__ double diag0[POD2G_MAX_K];
-    if (threadIdx.x == 0) fail = 0;
-    for (int j = threadIdx.x; j < k; j += blockDim.x) diag0[j] = Lout[j * k + j];
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-        if (threadIdx.x == 0) {
-            double d = Lout[j * k + j];
-            if (!(d > 64.0 * 2.220446049250313e-16 * diag0[j]) || !isfinite(d)) { fail = 1; d = 1.0; }
-            Lout[j * k + j] = sqrt(d);
-        }
-        __syncthreads();
-        double ljj = Lout[j * k + j];
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) Lout[i * k + j] /= ljj;
-        __syncthreads();
-        int m = k - j - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            int i = j + 1 + e / m, t = j + 1 + e % m;
-            if (t <= i) Lout[i * k + t] -= Lout[i * k + j] * Lout[t * k + j];
-        }
-        __syncthreads();
-    }
-    for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
-        int i = pr / k, j = pr - i * k;
-        if (j > i) Lout[pr] = 0.0;
-    }
-    if (threadIdx.x == 0 && fail) atomicCAS(status, (int)POD2G_OK, (int)POD2G_NOT_SPD);
+    ac_reduce_factor(part, gridDim.x, k, Ac, Lout, status);
     last_cta_reset(counter);
 }
 
+
+// ---------------------------------------------------------------------------- K_c on the tensor cores
+// K_c = Phi^T W (W = K Phi, double-float) as a dense contraction over the n rows on the
+// 5th-generation tensor cores (tcgen05.mma, BF16 operands, FP32 accumulation in tensor
+// memory). Each FP32 operand is split into three BF16 pieces, x = x1 + x2 + x3 exactly
+// (8 significant bits each; for W the high word, its low word being below the kept
+// terms); the products x_p y_q with p + q <= 2 (six per K-step) carry every bit down to
+// ~2^-24 of each term, as the split-precision tensor-core products of Ootomo and Yokota
+// (2022) do. Per CTA: a contiguous range of rows, in stages of TC_KT rows; the threads
+// load a stage, split it and store the pieces into shared memory in the no-swizzle
+// K-major layout (8 x 16-byte core matrices), one thread issues the MMAs of the stage
+// (TC_KT / 16 K-steps x 6 products) into one 128 x N FP32 accumulator in tensor memory
+// and commits them to an mbarrier, and the stage buffer is refilled only after that
+// barrier fires (two buffers). At the end each warp reads its 32 accumulator rows
+// (tcgen05.ld), the CTA writes its FP64 partial and the last CTA reduces and factors as
+// k_ac does. The accumulator sums at most rows-per-CTA terms in FP32.
+#define TC_KT 64                // rows per stage
+#define TC_M 128                // MMA rows (modes of Phi; rows >= k are zero)
+#define TC_THREADS 128          // four warps: one per 32-lane quarter of tensor memory
+#define TC_NP 3                 // BF16 pieces per operand
+
+__device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; lbo = byte distance of core
+// matrices adjacent along K, sbo = along M / N
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of tcgen05
+    return d;                // base offset 0, layout type 0 (no swizzle)
+}
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, unsigned parity) {
+    const uint32_t a = s_addr(bar);
+    for (unsigned t = 0; t < (1u << 22); ++t) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// three BF16 pieces of an FP32 value (exact: x = p0 + p1 + p2)
+__device__ __forceinline__ void bf16_split3(float x, __nv_bfloat16 (&p)[TC_NP]) {
+    p[0] = __float2bfloat16_rn(x);
+    const float r1 = __fsub_rn(x, __bfloat162float(p[0]));
+    p[1] = __float2bfloat16_rn(r1);
+    p[2] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(p[1])));
+}
+
+// shared-memory bytes of k_ac_tc for N accumulator columns
+__host__ __device__ constexpr size_t tc_smem_a() { return (size_t)TC_NP * TC_KT * TC_M * 2; }
+__host__ __device__ constexpr size_t tc_smem_b(int N) { return (size_t)TC_NP * TC_KT * N * 2; }
+static size_t tc_smem(int N) { return 2 * (tc_smem_a() + tc_smem_b(N)) + 64; }
+
+__global__ void __launch_bounds__(TC_THREADS)
+k_ac_tc(const float* __restrict__ phi, const float2* __restrict__ W, long long n, int k, int kp, int N,
+        double* __restrict__ part, unsigned* counter, double* __restrict__ Ac, double* __restrict__ Lout,
+        int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    // [buffer][piece][K/8][M/8][8 rows x 16 B] for A = Phi^T, [buffer][piece][K/8][N/8][128 B] for B = W
+    unsigned char* sA = tc_raw;
+    unsigned char* sB = tc_raw + 2 * tc_smem_a();
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_raw + 2 * (tc_smem_a() + tc_smem_b(N)));
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t LBO_A = (TC_M / 8) * 128, LBO_B = (uint32_t)(N / 8) * 128;
+    const size_t PIECE_A = (size_t)(TC_KT / 8) * LBO_A, PIECE_B = (size_t)(TC_KT / 8) * LBO_B;
+    // zero both buffers once: rows of A beyond k and columns of B beyond k stay zero
+    for (size_t e = tid; e < 2 * (tc_smem_a() + tc_smem_b(N)) / 16; e += TC_THREADS)
+        reinterpret_cast<uint4*>(tc_raw)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bars)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bars + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(s_addr(s_taddr))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_taddr;
+    const uint32_t idesc = tc_idesc(TC_M, N);
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long r0 = min(n, (long long)blockIdx.x * per), r1 = min(n, r0 + per);
+    const int nst = (int)((r1 - r0 + TC_KT - 1) / TC_KT);
+    bool bad = false;
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (st >= 2 && !tc_wait(bars + buf, (unsigned)((st - 2) >> 1) & 1u)) bad = true;
+        const long long base = r0 + (long long)st * TC_KT;
+        unsigned char* A = sA + buf * tc_smem_a();
+        unsigned char* B = sB + buf * tc_smem_b(N);
+        // two consecutive rows of one mode per item: a 32-bit word (two K positions) per piece
+        for (int e = tid; e < (TC_KT / 2) * kp; e += TC_THREADS) {
+            const int q = e / kp, m = e - q * kp;
+            if (m >= k) continue;
+            const int kk = 2 * q;
+            const long long i0 = base + kk, i1 = i0 + 1;
+            const float f0 = i0 < r1 ? __ldg(phi + i0 * kp + m) : 0.f;
+            const float f1 = i1 < r1 ? __ldg(phi + i1 * kp + m) : 0.f;
+            const float w0 = i0 < r1 ? W[i0 * kp + m].x : 0.f;
+            const float w1 = i1 < r1 ? W[i1 * kp + m].x : 0.f;
+            __nv_bfloat16 a0[TC_NP], a1[TC_NP], b0[TC_NP], b1[TC_NP];
+            bf16_split3(f0, a0);
+            bf16_split3(f1, a1);
+            bf16_split3(w0, b0);
+            bf16_split3(w1, b1);
+            const uint32_t in_core = (uint32_t)((m & 7) * 16 + (kk & 7) * 2);
+            const size_t offA = (size_t)(kk >> 3) * LBO_A + (size_t)(m >> 3) * 128 + in_core;
+            const size_t offB = (size_t)(kk >> 3) * LBO_B + (size_t)(m >> 3) * 128 + in_core;
+#pragma unroll
+            for (int p = 0; p < TC_NP; ++p) {
+                __nv_bfloat162 va, vb;
+                va.x = a0[p]; va.y = a1[p];
+                vb.x = b0[p]; vb.y = b1[p];
+                *reinterpret_cast<__nv_bfloat162*>(A + p * PIECE_A + offA) = va;
+                *reinterpret_cast<__nv_bfloat162*>(B + p * PIECE_B + offB) = vb;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = s_addr(A), b0 = s_addr(B);
+#pragma unroll
+            for (int ks = 0; ks < TC_KT / 16; ++ks) {
+#pragma unroll
+                for (int p = 0; p < TC_NP; ++p)
+#pragma unroll
+                    for (int q = 0; q + p < TC_NP; ++q) {
+                        const uint64_t da = tc_desc(a0 + (uint32_t)(p * PIECE_A) + 2 * ks * LBO_A, LBO_A, 128);
+                        const uint64_t db = tc_desc(b0 + (uint32_t)(q * PIECE_B) + 2 * ks * LBO_B, LBO_B, 128);
+                        tc_mma(tmem, da, db, idesc, (st > 0 || ks > 0 || p > 0 || q > 0) ? 1u : 0u);
+                    }
+            }
+            tc_commit(bars + buf);
+        }
+    }
+    // wait for the last stage's MMAs (a commit tracks every earlier MMA of the thread)
+    if (nst > 0 && !tc_wait(bars + ((nst - 1) & 1), (unsigned)((nst - 1) >> 1) & 1u)) bad = true;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // accumulator rows 32*warp .. 32*warp+31 (modes m1), columns m2 < N
+    const int m1 = warp * 32 + (tid & 31);
+    double* prt = part + (long long)blockIdx.x * k * k;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m1 < k)
+            for (int j = 0; j < 16 && c0 + j < k; ++j)
+                prt[(long long)m1 * k + c0 + j] = nst > 0 ? (double)__uint_as_float(v[j]) : 0.0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+    if (bad && tid == 0) atomicCAS(status, (int)POD2G_OK, (int)POD2G_TIMEOUT);
+    if (!last_cta_arrive(counter)) return;
+    ac_reduce_factor(part, gridDim.x, k, Ac, Lout, status);
+    last_cta_reset(counter);
+}
 }  // namespace
 
 // Mixed paths: D^-1, K Phi, K_c and its Cholesky factor from the slot's FP32 values in d_stage32.
@@ -286,9 +480,17 @@ static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
         k_w_df8<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, stage32, c->d_phi32, c->nb,
                                                       c->bs, c->kp, (float2*)c->d_W);
         P2G_TRY(pod2g_check_launch(c));
-        int ga = std::max(1, std::min(2 * c->num_sms, ceil_div(n, 256)));
-        k_ac<true><<<ga, T, 0, c->stream>>>(c->d_phi32, c->d_W, n, c->k, c->kp, c->d_ac_part,
-                                            c->d_counters + CNT_AC, c->d_Ac, L, st);
+        if (c->coarse_tc) {
+            // tensor cores: one CTA per SM (at least 4 stages each), N = k rounded up to 16
+            const int N = (c->k + 15) / 16 * 16;
+            const int ga = std::max(1, std::min(c->num_sms, ceil_div(n, 4 * TC_KT)));
+            k_ac_tc<<<ga, TC_THREADS, tc_smem(N), c->stream>>>(c->d_phi32, (const float2*)c->d_W, n, c->k, c->kp, N,
+                                                               c->d_ac_part, c->d_counters + CNT_AC, c->d_Ac, L, st);
+        } else {
+            const int ga = std::max(1, std::min(2 * c->num_sms, ceil_div(n, 256)));
+            k_ac<true><<<ga, T, 0, c->stream>>>(c->d_phi32, c->d_W, n, c->k, c->kp, c->d_ac_part,
+                                                c->d_counters + CNT_AC, c->d_Ac, L, st);
+        }
         P2G_TRY(pod2g_check_launch(c));
     }
     return POD2G_OK;
@@ -385,5 +587,12 @@ int setup_values(pod2g_ctx* c, int slot, const double* vals_dev, bool lane_done)
         P2G_TRY(pod2g_check_launch(c));
         P2G_TRY(setup_from_stage32(c, slot, st));
     }
+    return POD2G_OK;
+}
+
+// dynamic shared memory of the tensor-core contraction (once per context)
+int setup_tc_attributes(pod2g_ctx* c) {
+    const int N = (c->k + 15) / 16 * 16;
+    P2G_CUDA(cudaFuncSetAttribute(k_ac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(N)));
     return POD2G_OK;
 }

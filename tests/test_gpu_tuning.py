@@ -69,7 +69,7 @@ def test_shapes_deterministic_and_within_tolerance(pkg):
     P, Phi = wl.problem, pod_basis(wl)
     m = wl.spec.batch
     Bm = wl.rhs(m)
-    small = dict(grid_rows=8, grid_restrict=8, grid_prol=1, grid_vec=1, grid_spmv=16)
+    small = dict(grid_rows=8, grid_restrict=8, grid_prol=1, grid_vec=1, grid_spmv=16, rows_kernel=0)
     res = []
     for shape in (small, small, None):
         s, vals = _solver(pkg, wl, Phi, m)
@@ -92,8 +92,41 @@ def test_invalid_shapes_rejected(pkg):
     assert s.set_tuning(grid_spmv=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_restrict=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_vec=10 ** 6) == pkg.INVALID_ARG
+    assert s.set_tuning(rows_kernel=4) == pkg.INVALID_ARG
     s.close()
     f = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64)
     with pytest.raises(pkg.Pod2gError):
         f.get_tuning()
     f.close()
+
+
+@pytest.mark.parametrize("name,m", [("q4_16", 3), ("q4_64", 7), ("hex8_16", 5), ("q1_32", 5), ("q4_16", 40),
+                                    ("hex8_8", 36), ("q1_32", 20)])
+def test_row_kernel_forms_match_oracle(pkg, name, m):
+    """The two forms of the sparse row kernels (one thread per block row and slot, or
+    warp-staged with bulk-copied values; either for the smoother passes and the outer
+    SpMV independently) give the oracle's result: relative x error <= 1e-6, iteration
+    counts within +-2, and each form is deterministic."""
+    wl = Workload(name)
+    P, Phi = wl.problem, pod_basis(wl)
+    Bm = wl.rhs(m)
+    phi_used = round_phi(Phi, "bf16" if wl.spec.phi_dtype == "bf16" else "f32")
+    prec = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
+    res = {}
+    for form in (0, 1, 2, 3, 3):
+        s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=prec, omega=wl.spec.omega, max_batch=m)
+        vals = [round_f32(wl.values(xi)) for xi in wl.query_thetas(m)]
+        for i in range(m):
+            assert s.set_values(i, vals[i]) == pkg.OK
+        assert s.set_tuning(rows_kernel=form) == pkg.OK
+        X, it, rel, st, rc = s.solve_batch(list(range(m)), Bm, tol=TOL, maxit=3000)
+        assert rc == pkg.OK and np.all(st == pkg.OK)
+        s.close()
+        if form in res:
+            assert np.array_equal(res[form][0], X) and list(res[form][1]) == list(it)
+        res[form] = (X, it)
+    for i in sorted({0, m - 1}):
+        ref = O.pod2g_pcg(P.csr(vals[i]), Bm[i], None, phi_used, wl.spec.omega, TOL, 3000)
+        for form, (X, it) in res.items():
+            assert abs(int(it[i]) - ref.iters) <= 2, (form, i, it[i], ref.iters)
+            assert _relerr(X[i], ref.x) <= 1e-6, (form, i, _relerr(X[i], ref.x))
