@@ -132,15 +132,16 @@ def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False, sgs=Fal
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of these kernels on the
-# workload named (profiles/launches_q4_512_b64.md); valid only for the kernel
-# versions that capture measured.
+# workload named, keyed by (workload, batch, operator, row-kernel form); valid only for the
+# kernel versions that capture measured (the per-thread row kernels, form 0, for q4_512).
 NCU_TRAFFIC = {
-    ("q4_512", 64, "assembled"): {"k_spmv": 3156.2e6, "k_smooth1": 2964.0e6, "k_post": 3100.1e6, "k_upd": 1569.2e6,
-                                  "k_restrict": 185.5e6, "k_prol": 568.5e6, "k_p": 615.7e6, "k_coarse": 1.0e6},
+    ("q4_512", 64, "assembled", 0): {"k_spmv": 3156.2e6, "k_smooth1": 2964.0e6, "k_post": 3100.1e6,
+                                     "k_upd": 1569.2e6, "k_restrict": 185.5e6, "k_prol": 568.5e6, "k_p": 615.7e6,
+                                     "k_coarse": 1.0e6},
 }
 
 
-NCU_SOURCE = {("q4_512", 64, "assembled"): "profiles/launches_q4_512_b64.md"}
+NCU_SOURCE = {("q4_512", 64, "assembled", 0): "profiles/launches_q4_512_b64.md"}
 
 
 def run_oracle(mode, inst, timeout=900, workload=WORKLOAD, tol=TOL, method="pcg", smoother="jacobi"):
@@ -340,7 +341,7 @@ class WorkloadRun:
     """One workload on this rank: its POD basis, B instances' FP64 inputs resident in HBM, and a
     solver context (optionally under an HBM admission budget)."""
 
-    def __init__(self, args, pkg, name, B, rank=0, hbm_budget=0, autotune=True):
+    def __init__(self, args, pkg, name, B, rank=0, hbm_budget=0, autotune=True, surrogate=False):
         import torch
         from synth.problems import Workload
         from synth.snapshots import pod_basis
@@ -349,6 +350,11 @@ class WorkloadRun:
         P = self.P = wl.problem
         self.B = B
         t0 = time.time()
+        self.sur_w = None
+        if surrogate or args.x0 == "sur":
+            # the surrogate's training data and the solver's basis from one snapshot pass (offline)
+            from synth.surrogate import train_surrogate
+            self.sur_w = train_surrogate(wl, steps=2000, device="cuda")
         self.Phi = pod_basis(wl, device="cuda")
         self.t_phi = time.time() - t0
         self.xis = wl.query_thetas(B, offset=replica_offset(rank, B))   # distinct instances per rank
@@ -371,7 +377,13 @@ class WorkloadRun:
         self.slots = list(range(B))
         self.set_batch = self.s.set_coeffs_batch_dev if self.elements else self.s.set_values_batch_dev
         self.set_one = self.s.set_coeffs if self.elements else self.s.set_values
-        self.x0_dev = torch.empty_like(self.b_dev) if args.x0 == "rom" else None
+        self.x0_mode = args.x0
+        self.x0_dev = torch.empty_like(self.b_dev) if (args.x0 != "zero" or self.sur_w is not None) else None
+        self.sur = None
+        if self.sur_w is not None:
+            from synth.surrogate import load_scale
+            self.sur = pkg.Surrogate(self.sur_w, stream=self.stream.cuda_stream)
+            self.scales = np.array([load_scale(wl, b) for b in wl.rhs(B, offset=replica_offset(rank, B))])
         self.tuning = None
         if args.tuning:
             # a given launch shape (e.g. the one an earlier autotuned run reported), no autotuning
@@ -390,10 +402,16 @@ class WorkloadRun:
         pkg, s = self.pkg, self.s
         st, _ = self.set_batch(self.slots, self.vals)
         assert st == pkg.OK, pkg.strerror(st)
-        if self.x0_dev is not None:   # POD reduced-order solution as the initial guess
+        x0 = None
+        if self.x0_mode == "rom":     # POD reduced-order solution as the initial guess
             st = s.rom_solution_dev(self.slots, self.b_dev, self.x0_dev)
             assert st == pkg.OK, pkg.strerror(st)
-        iters, rel, status, rc = s.solve_batch_dev(self.slots, self.b_dev, self.x_dev, x0_dev=self.x0_dev,
+            x0 = self.x0_dev
+        elif self.x0_mode == "sur":   # surrogate prediction from each instance's parameters
+            st = self.sur.predict_dev(self.xis, self.scales, self.x0_dev)
+            assert st == pkg.OK, pkg.strerror(st)
+            x0 = self.x0_dev
+        iters, rel, status, rc = s.solve_batch_dev(self.slots, self.b_dev, self.x_dev, x0_dev=x0,
                                                    tol=self.args.tol, maxit=self.args.maxit)
         assert rc == pkg.OK, (pkg.strerror(rc), status)
         return iters, rel
@@ -450,7 +468,7 @@ class WorkloadRun:
         rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
         dom = max(ktimes, key=lambda k: ktimes[k][0])
         tot_k = sum(v[0] for v in ktimes.values())
-        key = (wl.spec.name, B, self.args.operator)
+        key = (wl.spec.name, B, self.args.operator, int(tun.get("rows_kernel", 0)))
         row = ("k_spmv", "k_smooth1", "k_post")
         return {"bound": "hbm", "kernel": dom, "achieved": rates[dom], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": rates[dom] / peaks["hbm_gbs"], "peak_kind": peak_kind,
@@ -479,7 +497,9 @@ class WorkloadRun:
     def close(self):
         import torch
         self.s.close()
-        del self.vals, self.b_dev, self.x_dev
+        if self.sur is not None:
+            self.sur.close()
+        del self.vals, self.b_dev, self.x_dev, self.x0_dev
         torch.cuda.empty_cache()
 
 
@@ -509,7 +529,8 @@ def gb300_arm(args):
     from synth.problems import SPECS
     B = args.batch or SPECS[args.workload].batch
     budget = args.hbm_budget_gb * 1e9 if args.workload == WORKLOAD else 0
-    run = WorkloadRun(args, pkg, args.workload, B, rank, hbm_budget=budget)
+    run = WorkloadRun(args, pkg, args.workload, B, rank, hbm_budget=budget,
+                      surrogate=(world == 1 and not args.no_surrogate and args.method == "pcg"))
     wl, P = run.wl, run.P
     sampler = ClockSampler(local)
     t = run.timed(args.steps, args.warmup, dist, sampler)
@@ -520,6 +541,18 @@ def gb300_arm(args):
     device_bytes = run.s.device_bytes()
 
     extra = {}
+    if run.sur is not None and args.x0 == "zero":
+        # the same steps with the surrogate's prediction as x0 (Section 3.2 then Algorithm 3)
+        run.x0_mode = "sur"
+        ts = run.timed(max(1, min(args.steps, 2)), 1)
+        run.x0_mode = "zero"
+        sw = run.sur_w
+        extra["x0_surrogate"] = {
+            "value": job_value(ts["ms"], 1, B), "unit": "solves/s", "ms_per_step": ts["ms"],
+            "iters_mean": float(np.mean(ts["iters"])), "iters_max": int(np.max(ts["iters"])),
+            "relres_max": float(np.max(ts["relres"])), "zero_x0_iters_mean": float(np.mean(t["iters"])),
+            "zero_x0_value": value, "latent_modes": int(sw.psi.shape[1]), "hidden": int(sw.w1.shape[0]),
+            "training_snapshots": wl.spec.n_snap, "latent_val_rel_err": sw.val_rel_err}
     if rank == 0 and world == 1:
         s, slots, tol, maxit = run.s, run.slots, args.tol, args.maxit
         # end to end through the C ABI with host buffers (values, b in; x out)
@@ -531,7 +564,13 @@ def gb300_arm(args):
         for _ in range(e2e_steps):
             for i in slots:
                 assert run.set_one(i, vals_h[i]) == pkg.OK
-            if run.x0_dev is None:
+            if run.x0_mode == "sur":
+                bd = torch.from_numpy(b_h).to(run.b_dev.device)
+                assert run.sur.predict_dev(run.xis, run.scales, run.x0_dev) == pkg.OK
+                it_h, rel_h, st_h, rc = s.solve_batch_dev(slots, bd, run.x_dev, x0_dev=run.x0_dev, tol=tol,
+                                                          maxit=maxit)
+                X = run.x_dev.cpu().numpy()
+            elif run.x0_mode == "zero":
                 X, it_h, rel_h, st_h, rc = s.solve_batch(slots, b_h, tol=tol, maxit=maxit)
             else:   # the reduced-order initial guess lives on the device: copy b in, x out
                 bd = torch.from_numpy(b_h).to(run.b_dev.device)
@@ -657,9 +696,13 @@ def plain_baseline(run, pkg, vals_h, b_h, value, num_sms):
     plain_iter = 3 * (8 * nnz + 4 * nnz) + 8 * 13 * n + 2 * 8 * n * k
     it_mean = statistics.mean(its)
     per_solve = [t for t in times]
+    Bp = 1 << (run.B - 1).bit_length()
+    batched_iter = sum(kernel_bytes(wl, 0 if k == 0 else [v for v in (8, 16, 24, 32, 40, 48, 64) if v >= k][0],
+                                    1, 0, 8, Bp).values())
     return {"value": pv, "unit": "solves/s", "iters": its, "ratio_batched_over_plain": value / pv,
             "achieved_GBs": plain_iter * it_mean / statistics.mean(per_solve) / 1e9,
-            "bytes_per_iteration": plain_iter}
+            "bytes_per_iteration": plain_iter, "batched_bytes_per_instance_iteration": batched_iter,
+            "bytes_bound_ratio": plain_iter / batched_iter}
 
 
 def serve_latency(s, pkg, wl, vals_h, b_h, rate, nreq, tol=TOL, maxit=MAXIT):
@@ -694,6 +737,130 @@ def serve_latency(s, pkg, wl, vals_h, b_h, rate, nreq, tol=TOL, maxit=MAXIT):
             "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "throughput": nreq / wall}
 
 
+# ----------------------------------------------------------------------------- serving mix
+MIX = ("q4_512", "hex8_64", "q1_1024")
+
+
+def serve_mix(args):
+    """Poisson-arrival requests spread in equal thirds over three registered problems (2D elasticity
+    Q4 512^2, 3D elasticity Hex8 64^3, 2D diffusion Q1 1024^2 with k = 25), each with its own context
+    and continuous batching, admitted under one HBM budget; p50/p99 latency per problem at fractions
+    of the mix's saturated throughput. A request carries one of 8 prepared instances of its problem
+    (values and right-hand side in host memory), copied by the library at submission."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2207_02543_gb300 as pkg
+    from synth.problems import Workload
+    from synth.snapshots import pod_basis
+    ni = 8
+    mix = pkg.ServingMix(int(args.hbm_budget_gb * 1e9), max_queue=4096)
+    probs = {}
+    t0 = time.time()
+    for name in MIX:
+        wl = Workload(name)
+        P = wl.problem
+        phi = pod_basis(wl, device="cuda")
+        prec = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
+        st = mix.register(name, P.row_ptr, P.col_idx, P.bs, phi, precision=prec, omega=wl.spec.omega,
+                          max_batch=wl.spec.batch)
+        assert st == pkg.OK, (name, pkg.strerror(st))
+        xis = wl.query_thetas(ni)
+        vals = wl.values_torch(xis, device="cuda").reshape(ni, -1).cpu().numpy()
+        probs[name] = dict(wl=wl, vals=vals, b=wl.rhs(ni), batch=wl.spec.batch)
+        torch.cuda.empty_cache()
+    prep_s = time.time() - t0
+
+    def run(reqs):
+        """reqs: list of (time offset s, problem); returns per-problem latencies and the wall time."""
+        handles = []
+        t_start = time.perf_counter()
+        for k, (dt, name) in enumerate(reqs):
+            while time.perf_counter() - t_start < dt:
+                time.sleep(0.0002)
+            pr = probs[name]
+            st, h = mix.submit(name, pr["vals"][k % ni], pr["b"][k % ni], tol=args.tol, maxit=args.maxit)
+            assert st == pkg.OK, pkg.strerror(st)
+            handles.append((name, h))
+        lat = {name: [] for name in MIX}
+        pending = dict(enumerate(handles))
+        while pending:
+            for k, (name, h) in list(pending.items()):
+                st, r = mix.poll(h)
+                if st == pkg.OK:
+                    assert r["status"] == pkg.OK
+                    lat[name].append(r["latency_s"])
+                    del pending[k]
+            time.sleep(0.001)
+        return lat, time.perf_counter() - t_start
+
+    # saturated throughput of each problem alone: two batches' worth submitted at once (after a warm-up)
+    rate = {}
+    for name in MIX:
+        B = probs[name]["batch"]
+        run([(0.0, name)] * B)
+        lat, wall = run([(0.0, name)] * (2 * B))
+        rate[name] = 2 * B / wall
+    lam_sat = len(MIX) / sum(1.0 / r for r in rate.values())   # equal thirds sharing the device
+    rng = np.random.default_rng(3000)
+    loads = [float(v) for v in args.serve_loads.split(",")]
+    out = []
+    for f in loads:
+        lam = f * lam_sat
+        nreq = args.serve_requests or max(30, int(30 * lam))
+        gaps = rng.exponential(1.0 / lam, nreq)
+        names = [MIX[i] for i in rng.integers(0, len(MIX), nreq)]
+        lat, wall = run(list(zip(np.cumsum(gaps), names)))
+        per = {}
+        for name in MIX:
+            ls = sorted(lat[name])
+            if ls:
+                per[name] = {"requests": len(ls), "p50_ms": 1e3 * ls[len(ls) // 2],
+                             "p99_ms": 1e3 * ls[min(len(ls) - 1, int(0.99 * len(ls)))]}
+        out.append({"load": f, "arrival_rate_per_s": lam, "requests": nreq, "throughput": nreq / wall,
+                    "per_problem": per})
+    used = mix.used_bytes()
+    mix.close()
+    line = {"metric": f"serving mix: p50/p99 latency at rel. residual {fmt_tol(args.tol)} (batched POD-2G-PCG)",
+            "unit": "ms", "n_gpus": 1, "data": "synthetic", "dtype": "f32+df64",
+            "config": {"workload": "Poisson arrivals, equal thirds over " +
+                                   "; ".join(workload_desc(probs[n]["wl"], probs[n]["batch"], args.tol) for n in MIX),
+                       "hbm_budget_bytes": int(args.hbm_budget_gb * 1e9), "device_bytes": int(used),
+                       "prepare_s": round(prep_s, 1)},
+            "saturated_solves_per_s": rate, "mix_saturated_solves_per_s": lam_sat, "loads": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def fma_rates(args):
+    """Dense FP64 and FP32 (no tensor cores) GEMM throughput on this GPU through torch / cuBLAS: the
+    FP64 : FP32 rate ratio that decides whether the outer recurrences are carried in FP64 or in
+    double-float (pairs of FP32)."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    torch.backends.cudnn.allow_tf32 = False
+    out = {}
+    for name, dt, nn in (("fp64", torch.float64, 8192), ("fp32", torch.float32, 16384)):
+        a = torch.randn(nn, nn, device="cuda", dtype=dt)
+        b = torch.randn(nn, nn, device="cuda", dtype=dt)
+        for _ in range(2):
+            torch.mm(a, b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            torch.mm(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_tflops"] = 2.0 * nn ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+        del a, b
+    out["fp32_over_fp64"] = out["fp32_tflops"] / out["fp64_tflops"]
+    out["metric"] = "dense GEMM throughput, torch.mm (cuBLAS), TF32 off"
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -721,15 +888,24 @@ def main():
                     "e.g. rows=1216,spmv=1216,restrict=456,prol=608,vec=1216")
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "sgs"],
                     help="relaxation of the two-grid cycle: damped Jacobi or multicolour symmetric Gauss-Seidel")
-    ap.add_argument("--x0", default="zero", choices=["zero", "rom"],
-                    help="initial guess: zero, or the POD reduced-order solution Phi K_c^-1 Phi^T b")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-x0 comparison key")
+    ap.add_argument("--x0", default="zero", choices=["zero", "rom", "sur"],
+                    help="initial guess: zero, the POD reduced-order solution Phi K_c^-1 Phi^T b, or the "
+                         "surrogate's prediction from the parameters")
     ap.add_argument("--tol", type=float, default=TOL)
     ap.add_argument("--oracle-workers", type=int, default=0,
                     help="cap on the oracle processes of the CPU baseline (default: cores, bounded by host memory)")
     ap.add_argument("--maxit", type=int, default=MAXIT)
+    ap.add_argument("--serve-mix", action="store_true",
+                    help="serving latency over three registered problems under one HBM budget (separate line)")
+    ap.add_argument("--fma-rates", action="store_true", help="FP64 and FP32 dense GEMM throughput (separate line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.fma_rates:
+        return fma_rates(args)
+    if args.serve_mix:
+        return serve_mix(args)
     return gb300_arm(args)
 
 

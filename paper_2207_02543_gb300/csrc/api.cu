@@ -316,7 +316,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     ALLOC(c->d_setup_status, sizeof(int) * c->B);
     ALLOC(c->d_stage, sizeof(double) * std::max(tot, (long long)c->n_el));
     ALLOC(c->d_W, sizeof(double) * (std::max(3LL, n) * std::max(kp, 1) + 64));
-    ALLOC(c->d_ac_part, sizeof(double) * std::max(1, 2 * c->num_sms * k * k));
+    ALLOC(c->d_ac_part, sizeof(double) * std::max(1, 3 * c->num_sms * k * k));
     ALLOC(c->d_Ac, sizeof(double) * std::max(1, k * k));
     ALLOC(c->d_counters, sizeof(unsigned) * CNT_N);
     if (c->smoother == POD2G_SMOOTHER_SGS) {

@@ -292,7 +292,7 @@ __global__ void k_ac(const void* __restrict__ phi_v, const void* __restrict__ W_
 // barrier fires (two buffers). At the end each warp reads its 32 accumulator rows
 // (tcgen05.ld), the CTA writes its FP64 partial and the last CTA reduces and factors as
 // k_ac does. The accumulator sums at most rows-per-CTA terms in FP32.
-#define TC_KT 64                // rows per stage
+#define TC_KT 32                // rows per stage (72 KB of shared memory: three CTAs per SM)
 #define TC_M 128                // MMA rows (modes of Phi; rows >= k are zero)
 #define TC_THREADS 128          // four warps: one per 32-lane quarter of tensor memory
 #define TC_NP 3                 // BF16 pieces per operand
@@ -481,9 +481,9 @@ static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
                                                       c->bs, c->kp, (float2*)c->d_W);
         P2G_TRY(pod2g_check_launch(c));
         if (c->coarse_tc) {
-            // tensor cores: one CTA per SM (at least 4 stages each), N = k rounded up to 16
+            // tensor cores: three CTAs per SM (at least 4 stages each), N = k rounded up to 16
             const int N = (c->k + 15) / 16 * 16;
-            const int ga = std::max(1, std::min(c->num_sms, ceil_div(n, 4 * TC_KT)));
+            const int ga = std::max(1, std::min(3 * c->num_sms, ceil_div(n, 4 * TC_KT)));
             k_ac_tc<<<ga, TC_THREADS, tc_smem(N), c->stream>>>(c->d_phi32, (const float2*)c->d_W, n, c->k, c->kp, N,
                                                                c->d_ac_part, c->d_counters + CNT_AC, c->d_Ac, L, st);
         } else {

@@ -120,3 +120,38 @@ def pod_basis(wl: Workload, k: int | None = None, count: int | None = None, devi
             np.save(path, Phi)
     _MEMO[key] = Phi
     return Phi
+
+
+def surrogate_data(wl: Workload, ks: int, count: int | None = None, device: str | None = None,
+                   use_disk: bool = True):
+    """Training data of the surrogate (Section 3.2) from the workload's snapshot set: the first ks
+    left singular vectors Psi (n x ks, the decoder of a linear autoencoder) and the latent
+    coordinates Z = Psi^T U (ks x N) of the N snapshots, with their parameters. The solver's basis
+    Phi is the first k columns of the same factorisation (stored too if missing)."""
+    count = wl.spec.n_snap if count is None else count
+    key = ("sur", wl.spec.name, ks, count)
+    if key in _MEMO:
+        return _MEMO[key]
+    path = os.path.join(cache_dir(), f"sur_{wl.spec.name}_ks{ks}_N{count}.npz")
+    if use_disk and os.path.exists(path):
+        d = np.load(path)
+        out = (d["psi"], d["z"], d["theta"])
+    else:
+        U = snapshot_matrix(wl, count, device)
+        k = wl.spec.k
+        W = signed_left_singular(U, max(k, ks))
+        phi_path = os.path.join(cache_dir(), f"phi_{wl.spec.name}_k{k}_N{count}.npy")
+        if use_disk and not os.path.exists(phi_path):
+            np.save(phi_path, W[:, :k])
+        psi = W[:, :ks].copy()
+        if isinstance(U, np.ndarray):
+            z = psi.T @ U
+        else:
+            import torch
+            z = (torch.from_numpy(psi).to(U.device).T @ U).cpu().numpy()
+        del U, W
+        out = (psi, z, wl.snapshot_thetas(count))
+        if use_disk:
+            np.savez(path, psi=psi, z=z, theta=out[2])
+    _MEMO[key] = out
+    return out
