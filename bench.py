@@ -788,11 +788,14 @@ def serve_mix(args):
             for k, (name, h) in list(pending.items()):
                 st, r = mix.poll(h)
                 if st == pkg.OK:
-                    assert r["status"] == pkg.OK
+                    if r["status"] != pkg.OK:
+                        failed.append({"problem": name, "status": pkg.strerror(r["status"]), "iters": r["iters"]})
                     lat[name].append(r["latency_s"])
                     del pending[k]
             time.sleep(0.001)
         return lat, time.perf_counter() - t_start
+
+    failed = []
 
     # saturated throughput of each problem alone: two batches' worth submitted at once (after a warm-up)
     rate = {}
@@ -827,9 +830,10 @@ def serve_mix(args):
                                    "; ".join(workload_desc(probs[n]["wl"], probs[n]["batch"], args.tol) for n in MIX),
                        "hbm_budget_bytes": int(args.hbm_budget_gb * 1e9), "device_bytes": int(used),
                        "prepare_s": round(prep_s, 1)},
-            "saturated_solves_per_s": rate, "mix_saturated_solves_per_s": lam_sat, "loads": out}
+            "saturated_solves_per_s": rate, "mix_saturated_solves_per_s": lam_sat, "loads": out,
+            "failed_requests": failed[:20], "failed_count": len(failed)}
     print(json.dumps(line), flush=True)
-    return 0
+    return 0 if not failed else 1
 
 
 def fma_rates(args):

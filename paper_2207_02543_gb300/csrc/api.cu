@@ -63,6 +63,16 @@ static int pick_kp(int k) {
     return -1;
 }
 
+int allow_max_smem(const void* fn) {
+    int dev = 0, mx = 0;
+    P2G_CUDA(cudaGetDevice(&dev));
+    P2G_CUDA(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    P2G_CUDA(cudaFuncGetAttributes(&fa, fn));
+    P2G_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
+    return POD2G_OK;
+}
+
 extern "C" {
 
 void pod2g_default_opts(pod2g_opts* o) {

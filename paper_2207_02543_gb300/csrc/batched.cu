@@ -1722,7 +1722,6 @@ static void launch_post_ws(pod2g_ctx* c, Dims D, int want) {
                        c->d_y32, nullptr, c->d_s32, c->d_part, c->d_counters + CNT_POST, c->d_sc, c->d_err));
 }
 static int ws_set_attributes(pod2g_ctx* c) {
-    const int sm = (int)ws_smem(c->bs, c->Bp);
     const void* fns[3] = {nullptr, nullptr, nullptr};
 #define WS_FN(BS_, SPT_)                                                   \
     if (c->bs == BS_ && ws_spt(c->Bp) == SPT_) {                           \
@@ -1734,7 +1733,7 @@ static int ws_set_attributes(pod2g_ctx* c) {
 #undef WS_FN
     for (const void* f : fns) {
         if (!f) return POD2G_INVALID_ARG;
-        P2G_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        P2G_TRY(allow_max_smem(f));
     }
     return POD2G_OK;
 }
@@ -1848,10 +1847,11 @@ int batched_alloc(pod2g_ctx* c) {
 #undef FN_KP
 #undef FN_LB
         if (!fr) return POD2G_INVALID_ARG;
-        P2G_CUDA(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_r));
-        P2G_CUDA(cudaFuncSetAttribute(fp2, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
-        P2G_CUDA(cudaFuncSetAttribute(fp1, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
-        P2G_CUDA(cudaFuncSetAttribute(fp0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_p));
+        if (sm_r > 227 * 1024 || sm_p > 227 * 1024) return POD2G_INVALID_ARG;
+        P2G_TRY(allow_max_smem(fr));
+        P2G_TRY(allow_max_smem(fp2));
+        P2G_TRY(allow_max_smem(fp1));
+        P2G_TRY(allow_max_smem(fp0));
     }
     return POD2G_OK;
 }

@@ -348,6 +348,10 @@ int setup_values_batch(pod2g_ctx* c, int nslots, const int* slots, const double*
 int setup_coeffs(pod2g_ctx* c, int slot, const double* coef_dev);
 int setup_theta(pod2g_ctx* c, int slot, const double* theta_dev);
 int setup_tc_attributes(pod2g_ctx* c);
+// Allow a kernel the device's largest dynamic shared memory per block. The attribute belongs to the
+// function, not to a context, so every context sets the same value: a context that needs less can
+// never lower the limit below what another context's launches of the same kernel request.
+int allow_max_smem(const void* fn);
 // doubles describing one instance: matrix values, or element coefficients
 static inline size_t instance_len(const pod2g_ctx* c) {
     return c->elem ? (size_t)c->n_el : (size_t)c->nnzb * c->bs * c->bs;

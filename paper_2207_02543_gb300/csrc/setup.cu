@@ -43,7 +43,7 @@ __global__ void k_dinv(const V* __restrict__ vals, const int32_t* __restrict__ d
     if (dinv32) dinv32[(long long)d * Bp + slot] = (float)(1.0 / a);
 }
 
-// Several instances at once: FP64 values [nslots][tot] -> FP32 lanes slots[i] of the
+// Several instances at once (more than 8): FP64 values [nslots][tot] -> FP32 lanes slots[i] of the
 // interleaved array, through a 32 x 32 shared-memory tile so that both the reads
 // (along entries) and the writes (along slots) are coalesced.
 __global__ void k_interleave(const double* __restrict__ v64, long long tot, int nslots, const int* __restrict__ slots,
@@ -61,6 +61,25 @@ __global__ void k_interleave(const double* __restrict__ v64, long long tot, int 
         const int i = s0 + threadIdx.x;
         const long long e = e0 + k;
         if (i < nslots && e < tot) vals32[e * Bp + slots[i]] = tile[threadIdx.x][k];
+    }
+}
+
+// Few instances (<= 8): FP64 values [nslots][tot] -> FP32 lanes, a thread per entry e reading the
+// instances' e-th values (coalesced along e) and writing them to its lanes of row e.
+__global__ void k_interleave_few(const double* __restrict__ v64, long long tot, int nslots,
+                                 const int* __restrict__ slots, int Bp, float* __restrict__ vals32) {
+    int sl[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sl[i] = i < nslots ? slots[i] : 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < nslots) v[i] = __double2float_rn(v64[(long long)i * tot + e]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < nslots) vals32[e * Bp + sl[i]] = v[i];
     }
 }
 
@@ -544,8 +563,13 @@ int setup_values_batch(pod2g_ctx* c, int nslots, const int* slots, const double*
     if (batch) {
         int* d_slots = (int*)(c->d_mask + c->Bp);
         P2G_CUDA(cudaMemcpyAsync(d_slots, slots, sizeof(int) * nslots, cudaMemcpyHostToDevice, c->stream));
-        dim3 grid((unsigned)((tot + 31) / 32), (unsigned)((nslots + 31) / 32)), block(32, 8);
-        k_interleave<<<grid, block, 0, c->stream>>>(values_dev, tot, nslots, d_slots, c->Bp, c->d_vals32);
+        if (nslots <= 8) {
+            k_interleave_few<<<std::max(1, std::min(ceil_div(tot, 256), 8 * c->num_sms)), 256, 0, c->stream>>>(
+                values_dev, tot, nslots, d_slots, c->Bp, c->d_vals32);
+        } else {
+            dim3 grid((unsigned)((tot + 31) / 32), (unsigned)((nslots + 31) / 32)), block(32, 8);
+            k_interleave<<<grid, block, 0, c->stream>>>(values_dev, tot, nslots, d_slots, c->Bp, c->d_vals32);
+        }
         P2G_TRY(pod2g_check_launch(c));
     }
     for (int i = 0; i < nslots; ++i) P2G_TRY(setup_values(c, slots[i], values_dev + (size_t)i * tot, batch));
@@ -592,7 +616,6 @@ int setup_values(pod2g_ctx* c, int slot, const double* vals_dev, bool lane_done)
 
 // dynamic shared memory of the tensor-core contraction (once per context)
 int setup_tc_attributes(pod2g_ctx* c) {
-    const int N = (c->k + 15) / 16 * 16;
-    P2G_CUDA(cudaFuncSetAttribute(k_ac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(N)));
-    return POD2G_OK;
+    (void)c;
+    return allow_max_smem((const void*)k_ac_tc);
 }
