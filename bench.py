@@ -99,7 +99,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False, sgs=False):
+def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False, sgs=False, kphi=False):
     """Algorithmic HBM bytes per kernel of the batched iteration (values FP32, vectors
     double-float 8 B, s/y/D^-1 FP32 4 B, Phi FP32 read once per launch, col_idx
     once per launch, per-slot scalars and partials negligible). Element operator:
@@ -122,6 +122,11 @@ def kernel_bytes(wl, k_pad, lane_iters, launches, G, Bp, elements=False, sgs=Fal
     }
     shared = {"k_p": 0, "k_spmv": pat, "k_upd": 0, "k_smooth1": pat, "k_restrict": phi,
               "k_coarse": G // 8 * Bp * (k_pad + 2) * 8, "k_prol": phi, "k_post": pat}
+    if kphi:  # prolongation and post-smoothing in one pass from K Phi (timed as k_post)
+        per_lane["k_prol"] = 0
+        per_lane["k_post"] = n * (4 * k_pad + 8 + 4 + 4 + 4)
+        shared["k_prol"] = 0
+        shared["k_post"] = phi
     if sgs:   # timing groups: forward sweeps + residual; stored y1; backward sweeps + r^T s
         per_lane["k_smooth1"] = 2 * vals + n * (20 + 16)
         per_lane["k_prol"] = n * (4 + 4)
@@ -462,9 +467,10 @@ class WorkloadRun:
         kp = {0: 0}.get(wl.spec.k, [v for v in (0, 8, 16, 24, 32, 40, 48, 64) if v >= wl.spec.k][0])
         nl = {k: v[1] for k, v in ktimes.items()}
         sgs = self.args.smoother == "sgs"
-        kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp, self.elements, sgs)
+        kphi = bool(tun.get("rows_kernel", 0) & 4)
+        kb = kernel_bytes(wl, kp, lane_iters, nl["k_spmv"], G, Bp, self.elements, sgs, kphi)
         # the same bytes with every lane active in every launch (what one ncu capture of a launch sees)
-        kb_all = kernel_bytes(wl, kp, B, 1, G, Bp, self.elements, sgs)
+        kb_all = kernel_bytes(wl, kp, B, 1, G, Bp, self.elements, sgs, kphi)
         rates = {k: (kb[k] / (ktimes[k][0] / 1e3) / 1e9 if ktimes[k][0] > 0 else 0.0) for k in kb}
         dom = max(ktimes, key=lambda k: ktimes[k][0])
         tot_k = sum(v[0] for v in ktimes.values())
@@ -697,8 +703,9 @@ def plain_baseline(run, pkg, vals_h, b_h, value, num_sms):
     it_mean = statistics.mean(its)
     per_solve = [t for t in times]
     Bp = 1 << (run.B - 1).bit_length()
+    kphi = bool((run.s.get_tuning() or {}).get("rows_kernel", 0) & 4)
     batched_iter = sum(kernel_bytes(wl, 0 if k == 0 else [v for v in (8, 16, 24, 32, 40, 48, 64) if v >= k][0],
-                                    1, 0, 8, Bp).values())
+                                    1, 0, 8, Bp, kphi=kphi).values())
     return {"value": pv, "unit": "solves/s", "iters": its, "ratio_batched_over_plain": value / pv,
             "achieved_GBs": plain_iter * it_mean / statistics.mean(per_solve) / 1e9,
             "bytes_per_iteration": plain_iter, "batched_bytes_per_instance_iteration": batched_iter,

@@ -370,9 +370,13 @@ typedef struct {
     int32_t rows_kernel;    /* form of the sparse row kernels: bit 0 the smoother passes, bit 1 the
                                outer SpMV use the warp-staged kernels (each warp copies the matrix
                                values of its rows into shared memory with bulk asynchronous copies
-                               ahead of use); 0 = one thread per block row and slot. Non-zero only
-                               for assembled operators with 4..64 slot lanes and Jacobi relaxation
-                               (default there: 3). */
+                               ahead of use; assembled operators with 4..64 slot lanes and Jacobi
+                               relaxation); bit 2: the prolongation and post-smoothing run as one
+                               pass that forms K y2 = (r - r1) + (K Phi) e_c from K Phi stored per slot
+                               at set-up, without a sweep over the matrix (contexts that store K Phi:
+                               assembled, Jacobi with r1 = r2 = 1, K Phi smaller than the values and
+                               within the HBM budget). 0 = one thread per block row and slot, and the
+                               post-smoothing as a sweep. Default: every form the context supports. */
 } pod2g_tuning;
 
 /* Current shape (mixed contexts; FP64 contexts return POD2G_INVALID_ARG). */

@@ -111,11 +111,11 @@ const char* pod2g_strerror(int s) {
 }
 
 static void free_all(pod2g_ctx* c) {
-    void* ptrs[] = {c->d_row_ptr, c->d_col_idx, c->d_diag_blk, c->d_phi64, c->d_phi32, c->d_phi16, c->d_Lc,
+    void* ptrs[] = {c->d_row_ptr, c->d_col_idx, c->d_diag_blk, c->d_phi64, c->d_phi32, c->d_Lc,
                     c->d_setup_status, c->d_stage, c->d_stage32, c->d_W, c->d_ac_part, c->d_Ac, c->d_counters,
                     c->d_vals64, c->d_dinv64, c->d_x64, c->d_r64, c->d_s64, c->d_p64, c->d_q64, c->d_y64, c->d_t64,
                     c->d_w64, c->d_c64, c->d_part64, c->d_scal64, c->d_vals32, c->d_dinv32, c->d_xdf, c->d_rdf,
-                    c->d_pdf, c->d_qdf, c->d_bdf, c->d_b64, c->d_s32, c->d_y32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
+                    c->d_pdf, c->d_qdf, c->d_bdf, c->d_b64, c->d_s32, c->d_y32, c->d_W32, c->d_ec, c->d_part, c->d_cpart, c->d_sc,
                     c->d_mask, c->d_iob, c->d_iox, c->d_err, c->d_desc, c->d_rowel, c->d_kref32, c->d_coef32, c->d_cnodes, c->d_colour, c->d_modes, c->d_theta};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -326,7 +326,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
     ALLOC(c->d_setup_status, sizeof(int) * c->B);
     ALLOC(c->d_stage, sizeof(double) * std::max(tot, (long long)c->n_el));
     ALLOC(c->d_W, sizeof(double) * (std::max(3LL, n) * std::max(kp, 1) + 64));
-    ALLOC(c->d_ac_part, sizeof(double) * std::max(1, 3 * c->num_sms * k * k));
+    ALLOC(c->d_ac_part, sizeof(double) * std::max(1, 2 * c->num_sms * k * k));
     ALLOC(c->d_Ac, sizeof(double) * std::max(1, k * k));
     ALLOC(c->d_counters, sizeof(unsigned) * CNT_N);
     if (c->smoother == POD2G_SMOOTHER_SGS) {
@@ -365,6 +365,12 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
         ALLOC(c->d_b64, sizeof(double) * n * Bp);
         ALLOC(c->d_s32, sizeof(float) * n * Bp);
         ALLOC(c->d_y32, sizeof(float) * n * Bp);
+        // K Phi per slot, for the post-smoothing without a matrix sweep (k_postw), when it is smaller
+        // than the slot's matrix values and fits the budget; otherwise the context does without it
+        if (!c->elem && c->smoother == POD2G_SMOOTHER_JACOBI && c->pre == 1 && c->post == 1 && kp > 0 &&
+            (long long)n * kp < tot) {
+            if (dev_alloc(c, (void**)&c->d_W32, sizeof(float) * n * kp * Bp) != POD2G_OK) c->d_W32 = nullptr;
+        }
         ALLOC(c->d_ec, sizeof(float) * std::max(1, Bp * kp));
         ALLOC(c->d_part, sizeof(double) * Gmax * Bp * 2);
         ALLOC(c->d_cpart, sizeof(double) * (size_t)Gmax * Bp * std::max(1, kp));

@@ -1135,6 +1135,226 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
     if (threadIdx.x == 0) *counter = 0u;
 }
 
+// ---------------------------------------------------------------------------- single-instance row kernels
+// For one slot lane (Bp = 1) a block row's values are one contiguous run ([block][bs*bs]); a
+// thread per row would walk it alone with strided, uncoalesced loads. Here a group of LPR lanes
+// (32 for 3 x 3 blocks, 16 otherwise) owns a row: lane t takes blocks beg + t, beg + t + LPR, ...,
+// so a group reads the row's values as one coalesced run and all its gathers are in flight at
+// once; the bs partial sums are then combined across the group by a fixed butterfly of shuffles
+// (double-float additions for the SpMV), and lane a < bs writes output a. KIND as k_rows_ws.
+template <int BS, int KIND>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
+k_rows_v1(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+          const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ vin,
+          const float* __restrict__ yin, float2* __restrict__ qout, float* __restrict__ out, double* part,
+          unsigned* counter, SlotScalars* sc) {
+    constexpr int LPR = BS == 3 ? 32 : 16;
+    constexpr int BB = BS * BS;
+    __shared__ double s_tmp[POD2G_THREADS];
+    __shared__ double s_out[2 * POD2G_MAX_BP];
+    const int sub = threadIdx.x & (LPR - 1);
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+    const bool on = sc[0].state == want;
+    const float w = (float)D.omega;
+    float d1h = 0.f, d1l = 0.f, d2h = 0.f, d2l = 0.f;
+    const long long groups = (long long)gridDim.x * (POD2G_THREADS / LPR);
+    if (on) {
+        for (long long i = (long long)blockIdx.x * (POD2G_THREADS / LPR) + threadIdx.x / LPR; i < D.nb; i += groups) {
+            const int beg = __ldg(row_ptr + i), end = __ldg(row_ptr + i + 1);
+            float ah[BS], al[BS];
+#pragma unroll
+            for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
+            for (int blk = beg + sub; blk < end; blk += LPR) {
+                const int j = __ldg(col_idx + blk);
+                float v[BB];
+                const float* vb = vals + (long long)blk * BB;
+#pragma unroll
+                for (int e = 0; e < BB; ++e) v[e] = __ldg(vb + e);
+                if constexpr (KIND == 0) {
+                    float2 pj[BS];
+#pragma unroll
+                    for (int cc = 0; cc < BS; ++cc) pj[cc] = vin[(long long)j * BS + cc];
+#pragma unroll
+                    for (int a = 0; a < BS; ++a)
+#pragma unroll
+                        for (int cc = 0; cc < BS; ++cc) df_acc_fma(ah[a], al[a], v[a * BS + cc], pj[cc].x, pj[cc].y);
+                } else {
+                    float yj[BS];
+#pragma unroll
+                    for (int cc = 0; cc < BS; ++cc) {
+                        const long long o = (long long)j * BS + cc;
+                        yj[cc] = KIND == 1 ? w * dinv[o] * vin[o].x : yin[o];
+                    }
+#pragma unroll
+                    for (int a = 0; a < BS; ++a)
+#pragma unroll
+                        for (int cc = 0; cc < BS; ++cc) ah[a] = __fmaf_rn(v[a * BS + cc], yj[cc], ah[a]);
+                }
+            }
+            // combine the group's partial sums (fixed butterfly; every lane ends with the totals)
+#pragma unroll
+            for (int off = LPR / 2; off > 0; off >>= 1) {
+#pragma unroll
+                for (int a = 0; a < BS; ++a) {
+                    const float oh = __shfl_xor_sync(gmask, ah[a], off);
+                    if constexpr (KIND == 0) {
+                        const float ol = __shfl_xor_sync(gmask, al[a], off);
+                        const float2 t = df_add(df_norm(ah[a], al[a]), df_norm(oh, ol));
+                        ah[a] = t.x;
+                        al[a] = t.y;
+                    } else {
+                        ah[a] = __fadd_rn(ah[a], oh);
+                    }
+                }
+            }
+            if (sub < BS) {
+                float h = ah[0], l = al[0];
+#pragma unroll
+                for (int a = 1; a < BS; ++a)
+                    if (sub == a) { h = ah[a]; l = al[a]; }
+                const long long o = (long long)i * BS + sub;
+                if constexpr (KIND == 0) {
+                    const float2 qv = df_norm(h, l);
+                    qout[o] = qv;
+                    const float2 pv = vin[o];
+                    df_acc_fma(d1h, d1l, pv.x, qv.x, qv.y);
+                    d1l = __fmaf_rn(pv.y, qv.x, d1l);
+                } else if constexpr (KIND == 1) {
+                    const float rv = vin[o].x;
+                    out[o] = rv - h;
+                    d1h = __fmaf_rn(rv, rv, d1h);
+                } else {
+                    const float2 rv = vin[o];
+                    const float sv = __fmaf_rn(w * dinv[o], rv.x - h, yin[o]);
+                    if (pr) df_acc_fma(d2h, d2l, out[o], rv.x, rv.y);
+                    out[o] = sv;
+                    df_acc_fma(d1h, d1l, sv, rv.x, rv.y);
+                }
+            }
+        }
+    }
+    cta_lane_sum((double)d1h + (double)d1l, 1, s_tmp, s_out);
+    if constexpr (KIND == 2) cta_lane_sum((double)d2h + (double)d2l, 1, s_tmp, s_out + 1);
+    cluster_store(s_out, KIND == 2 ? 2 : 1, part + (long long)(blockIdx.x / CLUSTER) * 2);
+    if constexpr (KIND == 1) return;
+    if (!last_cluster_arrive(counter, KIND == 0 ? D.NPs : D.NP)) return;
+    if constexpr (KIND == 0) {
+        const double pq = grid_lane_total(part, D.NPs, 2, 1, s_tmp);
+        if (threadIdx.x == 0) {
+            SlotScalars& S = sc[0];
+            if (S.state == want) {
+                if (S.iters >= S.maxit) {
+                    S.state = SLOT_DONE; S.result = POD2G_NOT_CONVERGED; S.alpha = 0.0;
+                } else if (!(pq > 0.0) || !isfinite(pq)) {
+                    S.state = SLOT_DONE; S.result = isfinite(pq) ? POD2G_BREAKDOWN : POD2G_NONFINITE; S.alpha = 0.0;
+                } else {
+                    S.alpha = D.stat ? 1.0 : S.rs / pq;
+                    S.iters += 1;
+                }
+            }
+        }
+    } else {
+        const double rs = grid_lane_total(part, D.NP, 2, 1, s_tmp);
+        const double rsx = pr ? grid_lane_total(part + 1, D.NP, 2, 1, s_tmp) : 0.0;
+        if (threadIdx.x == 0) {
+            SlotScalars& S = sc[0];
+            if (S.state == want) {
+                if (!(rs > 0.0) || !isfinite(rs)) {
+                    S.state = SLOT_DONE;
+                    S.result = isfinite(rs) ? POD2G_BREAKDOWN : POD2G_NONFINITE;
+                } else {
+                    S.beta = (S.first || D.stat) ? 0.0 : (pr ? (rs - rsx) / S.rs : rs / S.rs);
+                    S.rs = rs;
+                    S.first = 0;
+                    if (want == SLOT_JOINING) S.state = SLOT_ACTIVE;
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ---------------------------------------------------------------------------- prolongation + post-smoothing from K Phi
+// With W = K Phi of each slot stored (FP32, [n][KP][Bp], formed at set-up with K_c), the product
+// K y2 of the post-smoothing needs no pass over the matrix: y2 = y1 + Phi e_c, and
+// K y2 = K y1 + W e_c = (r - r1) + W e_c, since the pre-smoothing pass left r1 = r - K y1. Hence
+//     s = y2 + omega D^-1 (r - K y2) = y2 + omega D^-1 (r1 - W e_c),
+// one elementwise pass reading Phi (shared by the slots), W, r1, r and D^-1 instead of the
+// prolongation pass plus a sweep over the slot's matrix values: 4 n KP bytes of W per slot
+// against 4 bs^2 nnzb of values. Partial r^T s (and r^T s_old for Polak-Ribiere) per cluster; the
+// last cluster forms beta exactly as the post-smoothing row kernel does (Jacobi, r1 = r2 = 1).
+template <int KP>
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, 4)
+k_postw(Dims D, int want, int pr, const float* __restrict__ dinv, const float2* __restrict__ r,
+        const float* __restrict__ r1, const float* __restrict__ phi, const float* __restrict__ W,
+        const float* __restrict__ ec, float* __restrict__ s, double* part, unsigned* counter, SlotScalars* sc,
+        long long n) {
+    extern __shared__ float s_ec[];  // [Bp][KP + 1]
+    __shared__ double s_tmp[POD2G_THREADS];
+    __shared__ double s_out[2 * POD2G_MAX_BP];
+    for (int e = threadIdx.x; e < D.Bp * KP; e += blockDim.x) s_ec[(e / KP) * (KP + 1) + e % KP] = ec[e];
+    __syncthreads();
+    const int lane = threadIdx.x & (D.Bp - 1);
+    const bool on = sc[lane].state == want;
+    const float w = (float)D.omega;
+    float h = 0.f, l = 0.f, xh = 0.f, xl = 0.f;
+    if (on) {
+        const float* el = s_ec + lane * (KP + 1);   // the slot's e_c (odd row stride: no bank conflicts)
+        const long long items = n << D.lgBp;
+        for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+             it += (long long)gridDim.x * blockDim.x) {
+            const long long d = it >> D.lgBp;
+            const float4* ph = reinterpret_cast<const float4*>(phi + d * KP);
+            const float* wr = W + d * KP * D.Bp + lane;
+            const float2 rv = r[it];
+            const float dv = dinv[it];
+            const float r1v = r1[it];
+            const float so = pr ? s[it] : 0.f;
+            float y = w * dv * rv.x, y2 = 0.f, t = r1v, t2 = 0.f;
+#pragma unroll
+            for (int m4 = 0; m4 < KP / 4; ++m4) {
+                const float4 f = __ldg(ph + m4);
+                const float w0 = __ldg(wr + (4 * m4 + 0) * D.Bp), w1 = __ldg(wr + (4 * m4 + 1) * D.Bp);
+                const float w2 = __ldg(wr + (4 * m4 + 2) * D.Bp), w3 = __ldg(wr + (4 * m4 + 3) * D.Bp);
+                const float e0 = el[4 * m4], e1 = el[4 * m4 + 1], e2 = el[4 * m4 + 2], e3 = el[4 * m4 + 3];
+                y = __fmaf_rn(f.x, e0, y);
+                y2 = __fmaf_rn(f.y, e1, y2);
+                y = __fmaf_rn(f.z, e2, y);
+                y2 = __fmaf_rn(f.w, e3, y2);
+                t = __fmaf_rn(-w0, e0, t);
+                t2 = __fmaf_rn(-w1, e1, t2);
+                t = __fmaf_rn(-w2, e2, t);
+                t2 = __fmaf_rn(-w3, e3, t2);
+            }
+            const float sv = __fmaf_rn(w * dv, t + t2, y + y2);
+            if (pr) df_acc_fma(xh, xl, so, rv.x, rv.y);
+            s[it] = sv;
+            df_acc_fma(h, l, sv, rv.x, rv.y);
+        }
+    }
+    cta_lane_sum((double)h + (double)l, D.Bp, s_tmp, s_out);
+    cta_lane_sum((double)xh + (double)xl, D.Bp, s_tmp, s_out + D.Bp);
+    cluster_store(s_out, 2 * D.Bp, part + (long long)(blockIdx.x / CLUSTER) * D.Bp * 2);
+    if (!last_cluster_arrive(counter, D.NP)) return;
+    const double rs = grid_lane_total(part, D.NP, 2 * D.Bp, D.Bp, s_tmp);
+    const double rsx = pr ? grid_lane_total(part + D.Bp, D.NP, 2 * D.Bp, D.Bp, s_tmp) : 0.0;
+    if ((int)threadIdx.x < D.Bp) {
+        SlotScalars& S = sc[threadIdx.x];
+        if (S.state == want) {
+            if (!(rs > 0.0) || !isfinite(rs)) {
+                S.state = SLOT_DONE;
+                S.result = isfinite(rs) ? POD2G_BREAKDOWN : POD2G_NONFINITE;
+            } else {
+                S.beta = (S.first || D.stat) ? 0.0 : (pr ? (rs - rsx) / S.rs : rs / S.rs);
+                S.rs = rs;
+                S.first = 0;
+                if (want == SLOT_JOINING) S.state = SLOT_ACTIVE;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 // ---------------------------------------------------------------------------- warp-staged row kernels
 // The outer SpMV, the pre-smoothing pass and the post-smoothing pass of assembled
 // operators with 4 <= Bp <= 64 slot lanes and damped-Jacobi relaxation, restructured
@@ -1687,6 +1907,33 @@ static size_t ws_smem(int bs, int Bp) {
 }
 static bool ws_spmv(const pod2g_ctx* c) { return ws_applies(c) && (c->rows_kernel & 2); }
 static bool ws_smooth(const pod2g_ctx* c) { return ws_applies(c) && (c->rows_kernel & 1); }
+// single-instance contexts (Bp = 1): the group-per-row kernels are the alternative form
+static bool v1_applies(const pod2g_ctx* c) {
+    return !c->elem && c->precision != POD2G_FP64 && c->Bp == 1 && c->smoother == POD2G_SMOOTHER_JACOBI;
+}
+static bool v1_spmv(const pod2g_ctx* c) { return v1_applies(c) && (c->rows_kernel & 2); }
+static bool v1_smooth(const pod2g_ctx* c) { return v1_applies(c) && (c->rows_kernel & 1); }
+#define V1_DISPATCH(KIND, ...)                                                             \
+    do {                                                                                   \
+        if (c->bs == 1) k_rows_v1<1, KIND> __VA_ARGS__;                                    \
+        else if (c->bs == 2) k_rows_v1<2, KIND> __VA_ARGS__;                               \
+        else k_rows_v1<3, KIND> __VA_ARGS__;                                               \
+    } while (0)
+static void launch_spmv_v1(pod2g_ctx* c, Dims D, int want) {
+    V1_DISPATCH(0, <<<c->grid_spmv, POD2G_THREADS, 0, c->stream>>>(
+                       D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_pdf, nullptr,
+                       c->d_qdf, nullptr, c->d_part, c->d_counters + CNT_SPMV, c->d_sc));
+}
+static void launch_smooth1_v1(pod2g_ctx* c, Dims D, int want) {
+    V1_DISPATCH(1, <<<D.G, POD2G_THREADS, 0, c->stream>>>(
+                       D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_rdf, nullptr,
+                       nullptr, c->d_y32, c->d_part, nullptr, c->d_sc));
+}
+static void launch_post_v1(pod2g_ctx* c, Dims D, int want) {
+    V1_DISPATCH(2, <<<D.G, POD2G_THREADS, 0, c->stream>>>(
+                       D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_rdf,
+                       c->d_y32, nullptr, c->d_s32, c->d_part, c->d_counters + CNT_POST, c->d_sc));
+}
 
 #define WS_DISPATCH(KIND, ...)                                                            \
     do {                                                                                   \
@@ -1738,6 +1985,22 @@ static int ws_set_attributes(pod2g_ctx* c) {
     return POD2G_OK;
 }
 
+// Prolongation + post-smoothing from K Phi (k_postw): available when the context stores W (Jacobi
+// relaxation with r1 = r2 = 1), selected by bit 2 of rows_kernel.
+static bool kphi_post(const pod2g_ctx* c) { return c->d_W32 && (c->rows_kernel & 4); }
+static void launch_postw(pod2g_ctx* c, Dims D, int want) {
+    const size_t sm = sizeof(float) * c->Bp * (c->kp + 1);
+#define POSTW(KP_)                                                                                          \
+    case KP_:                                                                                               \
+        k_postw<KP_><<<D.G, POD2G_THREADS, sm, c->stream>>>(D, want, c->beta_pr, c->d_dinv32, c->d_rdf,   \
+                                                            c->d_y32, c->d_phi32, c->d_W32, c->d_ec,      \
+                                                            c->d_s32, c->d_part, c->d_counters + CNT_POST,  \
+                                                            c->d_sc, c->n);                                \
+        break;
+    switch (c->kp) { KP_LIST(POSTW) }
+#undef POSTW
+}
+
 // Event-record node after a kernel of a captured iteration (timing mode only).
 static int mark(pod2g_ctx* c) {
     P2G_TRY(pod2g_check_launch(c));
@@ -1756,17 +2019,26 @@ static int enqueue_precond(pod2g_ctx* c, Dims D, int want) {
     if (gs && c->pre) LAUNCH_BS(st = launch_gs, (c, D, want, 0));   // y1: forward sweep from zero, into s
     P2G_TRY(st);
     if (ws_smooth(c) && c->pre == 1) launch_smooth1_ws(c, D, want);
+    else if (v1_smooth(c) && c->pre == 1) launch_smooth1_v1(c, D, want);
     else LAUNCH_BS(launch_smooth1, (c, D, want));
     P2G_TRY(mark(c));
     if (c->kp > 0) launch_restrict(c, D, want);
     P2G_TRY(mark(c));
     k_coarse<<<c->Bp, POD2G_THREADS, 0, c->stream>>>(D, want, c->d_part, c->d_cpart, c->d_Lc, c->d_ec, c->d_sc);
     P2G_TRY(mark(c));
+    if (kphi_post(c)) {
+        // prolongation and post-smoothing in one pass from K Phi (timed as the post-smoothing)
+        if (c->cap_ev) P2G_CUDA(cudaEventRecordWithFlags(c->cap_ev[c->cap_idx++], c->stream, cudaEventRecordExternal));
+        launch_postw(c, D, want);
+        P2G_TRY(mark(c));
+        return POD2G_OK;
+    }
     launch_prol(c, D, want);
     P2G_TRY(mark(c));
     if (gs && c->post) LAUNCH_BS(st = launch_gs, (c, D, want, 1));  // backward sweep on s in place
     P2G_TRY(st);
     if (ws_smooth(c) && c->post == 1) launch_post_ws(c, D, want);
+    else if (v1_smooth(c) && c->post == 1) launch_post_v1(c, D, want);
     else LAUNCH_BS(launch_post, (c, D, want));
     P2G_TRY(mark(c));
     return POD2G_OK;
@@ -1782,6 +2054,8 @@ static int enqueue_iteration(pod2g_ctx* c, Dims D) {
     const ElemOp E = elem_op(c);
     if (ws_spmv(c))
         launch_spmv_ws(c, D, SLOT_ACTIVE);
+    else if (v1_spmv(c))
+        launch_spmv_v1(c, D, SLOT_ACTIVE);
     else
         LAUNCH_BS(k_spmv, <<<c->grid_spmv, POD2G_THREADS, 0, c->stream>>>(D, SLOT_ACTIVE, c->d_row_ptr, c->d_col_idx,
                                                                  c->d_vals32, E, c->d_pdf, c->d_qdf, c->d_part,
@@ -1802,7 +2076,21 @@ int batched_alloc(pod2g_ctx* c) {
     c->grid_restrict = batched_grid(c->num_sms, (long long)2 * c->num_sms * POD2G_THREADS);
     c->grid_prol = 8 * c->num_sms;
     c->grid_vec = 8 * c->num_sms;
-    c->rows_kernel = 0;
+    c->rows_kernel = c->d_W32 ? 4 : 0;
+    if (v1_applies(c)) {
+        // group-per-row kernels by default (single instance)
+        int occ = 0;
+        if (c->bs == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<1, 0>, POD2G_THREADS, 0);
+        else if (c->bs == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<2, 0>, POD2G_THREADS, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<3, 0>, POD2G_THREADS, 0);
+        cudaGetLastError();
+        if (occ > 0) {
+            c->rows_kernel |= 3;
+            c->ws_occ = occ;
+            c->grid_rows = std::max(CLUSTER, std::min(8 * c->num_sms, occ * c->num_sms) / CLUSTER * CLUSTER);
+            c->grid_spmv = c->grid_rows;
+        }
+    }
     if (ws_applies(c)) {
         // staged row kernels by default: one wave of resident CTAs for the row kernels
         P2G_TRY(ws_set_attributes(c));
@@ -1817,7 +2105,7 @@ int batched_alloc(pod2g_ctx* c) {
         if (occ > 0) {
             // four waves of resident CTAs (measured faster than one: the hardware keeps every SM
             // fed as 8-CTA clusters retire)
-            c->rows_kernel = 3;
+            c->rows_kernel |= 3;
             c->ws_occ = occ;
             c->grid_rows = std::max(CLUSTER, std::min(8 * c->num_sms, 4 * occ * c->num_sms) / CLUSTER * CLUSTER);
             c->grid_spmv = c->grid_rows;
@@ -1848,6 +2136,11 @@ int batched_alloc(pod2g_ctx* c) {
 #undef FN_LB
         if (!fr) return POD2G_INVALID_ARG;
         if (sm_r > 227 * 1024 || sm_p > 227 * 1024) return POD2G_INVALID_ARG;
+        const void* fw = nullptr;
+#define FW_KP(KP_) if (c->kp == KP_) fw = (const void*)k_postw<KP_>;
+        KP_LIST(FW_KP)
+#undef FW_KP
+        if (fw) P2G_TRY(allow_max_smem(fw));
         P2G_TRY(allow_max_smem(fr));
         P2G_TRY(allow_max_smem(fp2));
         P2G_TRY(allow_max_smem(fp1));
@@ -2057,7 +2350,9 @@ int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
     if (t->grid_spmv < CLUSTER || t->grid_spmv % CLUSTER || t->grid_spmv > 8 * sms) return POD2G_INVALID_ARG;
     if (t->grid_restrict < CLUSTER || t->grid_restrict % CLUSTER || t->grid_restrict > 4 * sms) return POD2G_INVALID_ARG;
     if (t->grid_prol < 1 || t->grid_prol > 8 * sms || t->grid_vec < 1 || t->grid_vec > 8 * sms) return POD2G_INVALID_ARG;
-    if (t->rows_kernel < 0 || t->rows_kernel > 3 || (t->rows_kernel && !(ws_applies(c) && c->ws_occ > 0)))
+    if (t->rows_kernel < 0 || t->rows_kernel > 7 ||
+        ((t->rows_kernel & 3) && !((ws_applies(c) || v1_applies(c)) && c->ws_occ > 0)) ||
+        ((t->rows_kernel & 4) && !c->d_W32))
         return POD2G_INVALID_ARG;
     c->rows_kernel = t->rows_kernel;
     c->grid_rows = t->grid_rows;
@@ -2094,14 +2389,15 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
         cand[j].grid_vec = std::min(vec_f[j] * sms, need_vec);
     }
     // the warp-staged row kernels (where they apply) with one to eight waves of resident CTAs
-    const bool ws = ws_applies(c) && c->ws_occ > 0;
+    const bool ws = (ws_applies(c) || v1_applies(c)) && c->ws_occ > 0;
     const int wave = c->ws_occ * sms;
     const int ws_f[NC] = {1, 2, 3, 4, 8};
     pod2g_tuning cand_ws[NC];
+    const int kbit = c->rows_kernel & 4;   // the K Phi form of the post-smoothing is kept as set
     for (int j = 0; j < NC; ++j) {
-        cand[j].rows_kernel = 0;
+        cand[j].rows_kernel = kbit;
         cand_ws[j] = cand[j];
-        cand_ws[j].rows_kernel = 3;
+        cand_ws[j].rows_kernel = 3 | kbit;
         cand_ws[j].grid_rows = r8(ws_f[j] * wave, 8 * sms);
         cand_ws[j].grid_spmv = cand_ws[j].grid_rows;
     }
@@ -2143,7 +2439,7 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
     const int br = best(t_rows, 2 * NC), bsp = best(t_spmv, 2 * NC);
     pick.grid_rows = row_cand(br).grid_rows;
     pick.grid_spmv = row_cand(bsp).grid_spmv;
-    pick.rows_kernel = (br >= NC ? 1 : 0) | (bsp >= NC ? 2 : 0);
+    pick.rows_kernel = (br >= NC ? 1 : 0) | (bsp >= NC ? 2 : 0) | (c->rows_kernel & 4);
     pick.grid_restrict = cand[best(t_res, NC)].grid_restrict;
     pick.grid_prol = cand[best(t_prol, NC)].grid_prol;
     pick.grid_vec = cand[best(t_vec, NC)].grid_vec;

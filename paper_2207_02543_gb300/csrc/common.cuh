@@ -74,8 +74,7 @@ struct pod2g_ctx {
 
     // POD basis, row-major [n][kp] (entries beyond k are zero)
     double* d_phi64 = nullptr;          // FP64 path
-    float* d_phi32 = nullptr;           // mixed paths (BF16-rounded values for MIXED_BF16PHI)
-    __nv_bfloat16* d_phi16 = nullptr;   // MIXED_BF16PHI: the basis as stored BF16
+    float* d_phi32 = nullptr;           // mixed paths (BF16-rounded values, widened, for MIXED_BF16PHI)
 
     // element-factored operator (pod2g_create_elements; elem = 1)
     int elem = 0, n_el = 0, npe = 0;
@@ -123,6 +122,7 @@ struct pod2g_ctx {
     double* d_b64 = nullptr;            // [n][Bp] the right-hand sides in FP64 (final residual)
     float* d_s32 = nullptr;             // [n][Bp]
     float* d_y32 = nullptr;             // [n][Bp]
+    float* d_W32 = nullptr;             // [n][kp][Bp] K Phi per slot (FP32), when the post-smoothing uses it
     float* d_ec = nullptr;              // [Bp][kp] coarse corrections
     double* d_part = nullptr;           // reduction partials [G][Bp][2] (scalars)
     double* d_cpart = nullptr;          // restriction partials [G][Bp][kp]

@@ -134,6 +134,16 @@ __global__ void k_w_f64(const int32_t* __restrict__ row_ptr, const int32_t* __re
     W[d * kp + m] = acc;
 }
 
+// W = K Phi (double-float [n][kp]) -> the slot's lane of the FP32 copy [n][kp][Bp] used by the
+// post-smoothing pass that forms K y2 from it
+__global__ void k_w32(const float2* __restrict__ W, long long total, int Bp, int slot, float* __restrict__ W32) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float2 w = W[e];
+        W32[e * Bp + slot] = __fadd_rn(w.x, w.y);
+    }
+}
+
 // Element coefficients (FP64, one instance) -> the slot's lane of the FP32
 // interleaved array; status NONFINITE on a NaN or Inf.
 __global__ void k_coef_convert(const double* __restrict__ c64, float* __restrict__ coef32, int n_el, int Bp,
@@ -304,14 +314,15 @@ __global__ void k_ac(const void* __restrict__ phi_v, const void* __restrict__ W_
 // terms); the products x_p y_q with p + q <= 2 (six per K-step) carry every bit down to
 // ~2^-24 of each term, as the split-precision tensor-core products of Ootomo and Yokota
 // (2022) do. Per CTA: a contiguous range of rows, in stages of TC_KT rows; the threads
-// load a stage, split it and store the pieces into shared memory in the no-swizzle
-// K-major layout (8 x 16-byte core matrices), one thread issues the MMAs of the stage
+// load a stage (issued while the previous one is being stored), split it and store the
+// pieces into shared memory in the no-swizzle K-major layout (8 x 16-byte core matrices),
+// one thread issues the MMAs of the stage
 // (TC_KT / 16 K-steps x 6 products) into one 128 x N FP32 accumulator in tensor memory
 // and commits them to an mbarrier, and the stage buffer is refilled only after that
 // barrier fires (two buffers). At the end each warp reads its 32 accumulator rows
 // (tcgen05.ld), the CTA writes its FP64 partial and the last CTA reduces and factors as
 // k_ac does. The accumulator sums at most rows-per-CTA terms in FP32.
-#define TC_KT 32                // rows per stage (72 KB of shared memory: three CTAs per SM)
+#define TC_KT 64                // rows per stage
 #define TC_M 128                // MMA rows (modes of Phi; rows >= k are zero)
 #define TC_THREADS 128          // four warps: one per 32-lane quarter of tensor memory
 #define TC_NP 3                 // BF16 pieces per operand
@@ -404,22 +415,38 @@ k_ac_tc(const float* __restrict__ phi, const float2* __restrict__ W, long long n
     const long long r0 = min(n, (long long)blockIdx.x * per), r1 = min(n, r0 + per);
     const int nst = (int)((r1 - r0 + TC_KT - 1) / TC_KT);
     bool bad = false;
+    // two consecutive rows of one mode per item (a 32-bit word, two K positions, per piece); a
+    // thread's items of the next stage are loaded into registers while the current one is stored
+    constexpr int TC_ITEMS = (TC_KT / 2) * POD2G_MAX_K / TC_THREADS;
+    const int nitems = (TC_KT / 2) * kp;
+    float pf[TC_ITEMS][4];
+    auto load_stage = [&](int st) {
+        const long long base = r0 + (long long)st * TC_KT;
+#pragma unroll
+        for (int u = 0; u < TC_ITEMS; ++u) {
+            const int e = tid + u * TC_THREADS;
+            const int q = e / kp, m = e - q * kp;
+            const long long i0 = base + 2 * q, i1 = i0 + 1;
+            const bool ok = e < nitems && m < k;
+            pf[u][0] = ok && i0 < r1 ? __ldg(phi + i0 * kp + m) : 0.f;
+            pf[u][1] = ok && i1 < r1 ? __ldg(phi + i1 * kp + m) : 0.f;
+            pf[u][2] = ok && i0 < r1 ? W[i0 * kp + m].x : 0.f;
+            pf[u][3] = ok && i1 < r1 ? W[i1 * kp + m].x : 0.f;
+        }
+    };
+    if (nst > 0) load_stage(0);
     for (int st = 0; st < nst; ++st) {
         const int buf = st & 1;
         if (st >= 2 && !tc_wait(bars + buf, (unsigned)((st - 2) >> 1) & 1u)) bad = true;
-        const long long base = r0 + (long long)st * TC_KT;
         unsigned char* A = sA + buf * tc_smem_a();
         unsigned char* B = sB + buf * tc_smem_b(N);
-        // two consecutive rows of one mode per item: a 32-bit word (two K positions) per piece
-        for (int e = tid; e < (TC_KT / 2) * kp; e += TC_THREADS) {
+#pragma unroll
+        for (int u = 0; u < TC_ITEMS; ++u) {
+            const int e = tid + u * TC_THREADS;
             const int q = e / kp, m = e - q * kp;
-            if (m >= k) continue;
+            if (e >= nitems || m >= k) continue;
             const int kk = 2 * q;
-            const long long i0 = base + kk, i1 = i0 + 1;
-            const float f0 = i0 < r1 ? __ldg(phi + i0 * kp + m) : 0.f;
-            const float f1 = i1 < r1 ? __ldg(phi + i1 * kp + m) : 0.f;
-            const float w0 = i0 < r1 ? W[i0 * kp + m].x : 0.f;
-            const float w1 = i1 < r1 ? W[i1 * kp + m].x : 0.f;
+            const float f0 = pf[u][0], f1 = pf[u][1], w0 = pf[u][2], w1 = pf[u][3];
             __nv_bfloat16 a0[TC_NP], a1[TC_NP], b0[TC_NP], b1[TC_NP];
             bf16_split3(f0, a0);
             bf16_split3(f1, a1);
@@ -437,6 +464,7 @@ k_ac_tc(const float* __restrict__ phi, const float2* __restrict__ W, long long n
                 *reinterpret_cast<__nv_bfloat162*>(B + p * PIECE_B + offB) = vb;
             }
         }
+        if (st + 1 < nst) load_stage(st + 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -499,10 +527,16 @@ static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
         k_w_df8<<<ceil_div(tw, T), T, 0, c->stream>>>(c->d_row_ptr, c->d_col_idx, stage32, c->d_phi32, c->nb,
                                                       c->bs, c->kp, (float2*)c->d_W);
         P2G_TRY(pod2g_check_launch(c));
+        if (c->d_W32) {
+            const long long tot = (long long)n * c->kp;
+            k_w32<<<std::max(1, std::min(ceil_div(tot, T), 8 * c->num_sms)), T, 0, c->stream>>>(
+                (const float2*)c->d_W, tot, c->Bp, slot, c->d_W32);
+            P2G_TRY(pod2g_check_launch(c));
+        }
         if (c->coarse_tc) {
-            // tensor cores: three CTAs per SM (at least 4 stages each), N = k rounded up to 16
+            // tensor cores: one CTA per SM (at least 4 stages each), N = k rounded up to 16
             const int N = (c->k + 15) / 16 * 16;
-            const int ga = std::max(1, std::min(3 * c->num_sms, ceil_div(n, 4 * TC_KT)));
+            const int ga = std::max(1, std::min(c->num_sms, ceil_div(n, 4 * TC_KT)));
             k_ac_tc<<<ga, TC_THREADS, tc_smem(N), c->stream>>>(c->d_phi32, (const float2*)c->d_W, n, c->k, c->kp, N,
                                                                c->d_ac_part, c->d_counters + CNT_AC, c->d_Ac, L, st);
         } else {

@@ -58,8 +58,10 @@ def test_element_path_matches_assembled_and_oracle(pkg, name, precision, method)
     kw = dict(precision=precision, omega=wl.spec.omega, max_batch=m, method=method)
     se = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, elements=_elements(P), **kw)
     sa = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, **kw)
-    # element contexts run the per-thread row kernels: compare with the same form of the assembled path
-    assert sa.set_tuning(rows_kernel=0) == pkg.OK
+    # element contexts run the per-thread row kernels: compare with the same form and launch shape
+    shape = se.get_tuning()
+    assert shape["rows_kernel"] == 0
+    assert sa.set_tuning(**shape) == pkg.OK
     vals = [_f32_values(P, c) for c in coefs]
     for i in range(m):
         assert se.set_coeffs(i, coefs[i]) == pkg.OK

@@ -92,7 +92,7 @@ def test_invalid_shapes_rejected(pkg):
     assert s.set_tuning(grid_spmv=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_restrict=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_vec=10 ** 6) == pkg.INVALID_ARG
-    assert s.set_tuning(rows_kernel=4) == pkg.INVALID_ARG
+    assert s.set_tuning(rows_kernel=8) == pkg.INVALID_ARG
     s.close()
     f = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64)
     with pytest.raises(pkg.Pod2gError):
@@ -101,19 +101,25 @@ def test_invalid_shapes_rejected(pkg):
 
 
 @pytest.mark.parametrize("name,m", [("q4_16", 3), ("q4_64", 7), ("hex8_16", 5), ("q1_32", 5), ("q4_16", 40),
-                                    ("hex8_8", 36), ("q1_32", 20)])
+                                    ("hex8_8", 36), ("q1_32", 20), ("q4_16", 1), ("hex8_16", 1), ("q1_32", 1)])
 def test_row_kernel_forms_match_oracle(pkg, name, m):
-    """The two forms of the sparse row kernels (one thread per block row and slot, or
-    warp-staged with bulk-copied values; either for the smoother passes and the outer
-    SpMV independently) give the oracle's result: relative x error <= 1e-6, iteration
-    counts within +-2, and each form is deterministic."""
+    """The forms of the sparse row kernels (one thread per block row and slot, or warp-staged
+    with bulk-copied values -- for a single slot, a group of lanes per block row -- for the
+    smoother passes and the outer SpMV independently; and,
+    where the context stores K Phi, the post-smoothing pass that forms K y2 from it) give the
+    oracle's result: relative x error <= 1e-6, iteration counts within +-2, and each form is
+    deterministic."""
     wl = Workload(name)
     P, Phi = wl.problem, pod_basis(wl)
     Bm = wl.rhs(m)
     phi_used = round_phi(Phi, "bf16" if wl.spec.phi_dtype == "bf16" else "f32")
     prec = pkg.MIXED_BF16PHI if wl.spec.phi_dtype == "bf16" else pkg.MIXED_FP32PHI
     res = {}
-    for form in (0, 1, 2, 3, 3):
+    probe = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=prec, omega=wl.spec.omega, max_batch=m)
+    kphi = probe.get_tuning()["rows_kernel"] & 4
+    probe.close()
+    forms = (0, 1, 2, 3, 4, 7, 7) if kphi else (0, 1, 2, 3, 3)
+    for form in forms:
         s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=prec, omega=wl.spec.omega, max_batch=m)
         vals = [round_f32(wl.values(xi)) for xi in wl.query_thetas(m)]
         for i in range(m):
