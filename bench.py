@@ -143,10 +143,16 @@ NCU_TRAFFIC = {
     ("q4_512", 64, "assembled", 0): {"k_spmv": 3156.2e6, "k_smooth1": 2964.0e6, "k_post": 3100.1e6,
                                      "k_upd": 1569.2e6, "k_restrict": 185.5e6, "k_prol": 568.5e6, "k_p": 615.7e6,
                                      "k_coarse": 1.0e6},
+    # staged SpMV and pre-smoothing captured on Hex8 64^3 with 4 slots, scaled to Hex8 128^3 by the
+    # stored blocks (57,066,625 / 7,189,057): profiles/traffic_k_rows_ws_hex8_b4.md
+    ("hex8_128", 4, "assembled", 7): {"k_spmv": 8.961e9, "k_smooth1": 9.049e9},
+    ("hex8_128", 4, "assembled", 3): {"k_spmv": 8.961e9, "k_smooth1": 9.049e9},
 }
 
 
-NCU_SOURCE = {("q4_512", 64, "assembled", 0): "profiles/launches_q4_512_b64.md"}
+NCU_SOURCE = {("q4_512", 64, "assembled", 0): "profiles/launches_q4_512_b64.md",
+              ("hex8_128", 4, "assembled", 7): "profiles/traffic_k_rows_ws_hex8_b4.md",
+              ("hex8_128", 4, "assembled", 3): "profiles/traffic_k_rows_ws_hex8_b4.md"}
 
 
 def run_oracle(mode, inst, timeout=900, workload=WORKLOAD, tol=TOL, method="pcg", smoother="jacobi"):
@@ -392,7 +398,7 @@ class WorkloadRun:
         self.tuning = None
         if args.tuning:
             # a given launch shape (e.g. the one an earlier autotuned run reported), no autotuning
-            shape = {(k if k == "rows_kernel" else f"grid_{k}"): int(v)
+            shape = {(k if k in ("rows_kernel", "restrict_rows") else f"grid_{k}"): int(v)
                      for k, v in (kv.split("=") for kv in args.tuning.split(","))}
             assert self.s.set_tuning(**shape) == pkg.OK, shape
             self.tuning = self.s.get_tuning()

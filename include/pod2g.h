@@ -377,6 +377,9 @@ typedef struct {
                                assembled, Jacobi with r1 = r2 = 1, K Phi smaller than the values and
                                within the HBM budget). 0 = one thread per block row and slot, and the
                                post-smoothing as a sweep. Default: every form the context supports. */
+    int32_t restrict_rows;  /* rows of Phi and r1 per shared-memory chunk of the bulk-staged
+                               restriction (its tile; multiple of 4, 4..256, within 200 KB of shared
+                               memory; 4 or more slot lanes); 0 = the default (~24 KB per chunk) */
 } pod2g_tuning;
 
 /* Current shape (mixed contexts; FP64 contexts return POD2G_INVALID_ARG). */
@@ -384,7 +387,7 @@ int pod2g_get_tuning(pod2g_t ctx, pod2g_tuning* out);
 /* Set a shape; POD2G_INVALID_ARG if a field is out of range or the context is serving. */
 int pod2g_set_tuning(pod2g_t ctx, const pod2g_tuning* t);
 /* Autotuner: for five candidate shapes (and, where they apply, five grid sizes of the
- * warp-staged row kernels), solve the given set-up slots with right-hand
+ * warp-staged row kernels, then half and twice the restriction's default chunk), solve the given set-up slots with right-hand
  * sides b_dev (nslots consecutive vectors of n doubles, device) for `iters`
  * iterations (rounded up to whole graph launches), timing each kernel with CUDA
  * events, and keep per kernel group the fastest candidate (kernel form and grid). The slots are left idle

@@ -508,6 +508,7 @@ int pod2g_get_tuning(pod2g_t c, pod2g_tuning* out) {
     out->grid_vec = c->grid_vec;
     out->grid_spmv = c->grid_spmv;
     out->rows_kernel = c->rows_kernel;
+    out->restrict_rows = c->restrict_rows;
     return POD2G_OK;
 }
 

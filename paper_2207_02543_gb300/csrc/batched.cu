@@ -1812,25 +1812,32 @@ static int restrict_grid(pod2g_ctx* c) { return c->grid_restrict; }
 // Bulk-staged restriction: rows per chunk (~24 KB of r1 and Phi per stage, a
 // multiple of 4) and its shared memory; 0 when it does not apply (Bp < 4: rows
 // of r1 are not 16-byte multiples) or does not fit.
-static int restrict_bulk_rows(int Bp, int kp) {
+static int restrict_bulk_rows_default(int Bp, int kp) {
     if (kp == 0 || Bp < 4) return 0;
     int R = 24576 / ((Bp + kp) * 4);
     R = std::max(8, std::min(128, R)) / 4 * 4;
     return R;
 }
-static size_t restrict_bulk_smem(int Bp, int kp) {
-    const int R = restrict_bulk_rows(Bp, kp);
+static size_t restrict_bulk_smem_rows(int Bp, int kp, int R) {
     if (R == 0) return 0;
     const size_t sz = restrict_smem(Bp, kp) + (size_t)RS_STAGES * R * (Bp + kp) * sizeof(float) +
                       RS_STAGES * sizeof(uint64_t);
     return sz <= 200 * 1024 ? sz : 0;
 }
+// the context's rows per chunk (a tuning setting; 0 = the default)
+static int restrict_bulk_rows(const pod2g_ctx* c) {
+    if (c->kp == 0 || c->Bp < 4) return 0;
+    return c->restrict_rows > 0 ? c->restrict_rows : restrict_bulk_rows_default(c->Bp, c->kp);
+}
+static size_t restrict_bulk_smem(const pod2g_ctx* c) {
+    return restrict_bulk_smem_rows(c->Bp, c->kp, restrict_bulk_rows(c));
+}
 
 #define LB_LIST(X, KP) X(KP, 1) X(KP, 2) X(KP, 4) X(KP, 8)
 static void launch_restrict(pod2g_ctx* c, Dims D, int want) {
-    const size_t smb = restrict_bulk_smem(c->Bp, c->kp);
+    const size_t smb = restrict_bulk_smem(c);
     const size_t sm = smb ? smb : restrict_smem(c->Bp, c->kp);
-    const int R = restrict_bulk_rows(c->Bp, c->kp);
+    const int R = restrict_bulk_rows(c);
     const int g = D.NPc * CLUSTER;
     const int lb = restrict_lb(c->Bp, c->kp);
 #define CASE_LB(KP_, LB_)                                                                                          \
@@ -2112,8 +2119,7 @@ int batched_alloc(pod2g_ctx* c) {
         }
     }
     if (c->precision != POD2G_FP64 && c->kp > 0) {
-        const int sm_r = (int)(restrict_bulk_smem(c->Bp, c->kp) ? restrict_bulk_smem(c->Bp, c->kp)
-                                                                 : restrict_smem(c->Bp, c->kp));
+        const int sm_r = (int)(restrict_bulk_smem(c) ? restrict_bulk_smem(c) : restrict_smem(c->Bp, c->kp));
         const int lb = restrict_lb(c->Bp, c->kp);
         const int sm_p = c->Bp * (c->kp + 1) * (int)sizeof(float);
         const void* fr = nullptr;
@@ -2122,8 +2128,8 @@ int batched_alloc(pod2g_ctx* c) {
         const void* fp0 = nullptr;
 #define FN_LB(KP_, LB_)                                                                    \
         if (c->kp == KP_ && lb == LB_)                                                     \
-            fr = restrict_bulk_smem(c->Bp, c->kp) ? (const void*)k_restrict_bulk<KP_, LB_> \
-                                                  : (const void*)k_restrict<KP_, LB_>;
+            fr = restrict_bulk_smem(c) ? (const void*)k_restrict_bulk<KP_, LB_> \
+                                       : (const void*)k_restrict<KP_, LB_>;
 #define FN_KP(KP_)                                                      \
         LB_LIST(FN_LB, KP_)                                              \
         if (c->kp == KP_) {                                              \
@@ -2354,6 +2360,15 @@ int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
         ((t->rows_kernel & 3) && !((ws_applies(c) || v1_applies(c)) && c->ws_occ > 0)) ||
         ((t->rows_kernel & 4) && !c->d_W32))
         return POD2G_INVALID_ARG;
+    if (t->restrict_rows != 0 &&
+        (t->restrict_rows < 4 || t->restrict_rows > 256 || t->restrict_rows % 4 || c->Bp < 4 || c->kp == 0 ||
+         !restrict_bulk_smem_rows(c->Bp, c->kp, t->restrict_rows)))
+        return POD2G_INVALID_ARG;
+    // a bulk-staged restriction stays bulk-staged (its kernel and attributes were chosen at creation)
+    if (t->restrict_rows == 0 && c->Bp >= 4 && c->kp > 0 &&
+        !restrict_bulk_smem_rows(c->Bp, c->kp, restrict_bulk_rows_default(c->Bp, c->kp)))
+        return POD2G_INVALID_ARG;
+    c->restrict_rows = t->restrict_rows;
     c->rows_kernel = t->rows_kernel;
     c->grid_rows = t->grid_rows;
     c->grid_spmv = t->grid_spmv;
@@ -2443,6 +2458,27 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
     pick.grid_restrict = cand[best(t_res, NC)].grid_restrict;
     pick.grid_prol = cand[best(t_prol, NC)].grid_prol;
     pick.grid_vec = cand[best(t_vec, NC)].grid_vec;
+    pick.restrict_rows = 0;
+    // the restriction's rows per staged chunk (its Phi / r1 tile): half, the default and twice
+    const int R0 = restrict_bulk_rows_default(c->Bp, c->kp);
+    if (R0 > 0) {
+        double best_t = t_res[best(t_res, NC)];
+        for (int f = 0; f < 2; ++f) {
+            const int R = f == 0 ? std::max(4, R0 / 2 / 4 * 4) : std::min(256, R0 * 2);
+            if (R == R0 || !restrict_bulk_smem_rows(c->Bp, c->kp, R)) continue;
+            pod2g_tuning tr = pick;
+            tr.restrict_rows = R;
+            P2G_TRY(batched_set_tuning(c, &tr));
+            P2G_TRY(batched_set_timing(c, 1));
+            P2G_TRY(batched_load(c, nslots, slots, b_dev, nullptr, tol.data(), maxit.data()));
+            for (int it = 0; it < iters; it += c->chunk) P2G_TRY(batched_chunk(c));
+            const double tr_ms = c->kt_n[4] ? c->kt_ms[4] / (double)c->kt_n[4] : 1e300;
+            if (tr_ms < best_t) {
+                best_t = tr_ms;
+                pick.restrict_rows = R;
+            }
+        }
+    }
     P2G_TRY(batched_set_tuning(c, &pick));
     P2G_TRY(batched_set_timing(c, timing0 ? 1 : 0));
     // leave the slots idle

@@ -143,6 +143,7 @@ struct pod2g_ctx {
     int grid_vec = 0;                   // CTAs of the vector updates (p, x/r)
     int rows_kernel = 0;                // bit 0: staged smoother row kernels, bit 1: staged outer SpMV
     int ws_occ = 0;                     // resident CTAs per SM of the staged row kernels (0: not available)
+    int restrict_rows = 0;              // rows per staged chunk of the restriction (0: default)
     cudaGraphExec_t graph_exec = nullptr;
     // per-kernel timing (event-record nodes around each kernel of the captured iterations)
     bool timing = false;

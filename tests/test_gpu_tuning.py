@@ -69,7 +69,8 @@ def test_shapes_deterministic_and_within_tolerance(pkg):
     P, Phi = wl.problem, pod_basis(wl)
     m = wl.spec.batch
     Bm = wl.rhs(m)
-    small = dict(grid_rows=8, grid_restrict=8, grid_prol=1, grid_vec=1, grid_spmv=16, rows_kernel=0)
+    small = dict(grid_rows=8, grid_restrict=8, grid_prol=1, grid_vec=1, grid_spmv=16, rows_kernel=0,
+                 restrict_rows=8)
     res = []
     for shape in (small, small, None):
         s, vals = _solver(pkg, wl, Phi, m)
@@ -93,6 +94,7 @@ def test_invalid_shapes_rejected(pkg):
     assert s.set_tuning(grid_restrict=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_vec=10 ** 6) == pkg.INVALID_ARG
     assert s.set_tuning(rows_kernel=8) == pkg.INVALID_ARG
+    assert s.set_tuning(restrict_rows=6) == pkg.INVALID_ARG       # not a multiple of 4
     s.close()
     f = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64)
     with pytest.raises(pkg.Pod2gError):
