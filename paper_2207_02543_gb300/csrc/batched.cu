@@ -2085,14 +2085,15 @@ int batched_alloc(pod2g_ctx* c) {
     c->grid_vec = 8 * c->num_sms;
     c->rows_kernel = c->d_W32 ? 4 : 0;
     if (v1_applies(c)) {
-        // group-per-row kernels by default (single instance)
+        // single instance: the group-per-row smoothing kernels by default (the per-thread SpMV was
+        // measured faster than the group-per-row one; the autotuner compares both forms)
         int occ = 0;
         if (c->bs == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<1, 0>, POD2G_THREADS, 0);
         else if (c->bs == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<2, 0>, POD2G_THREADS, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<3, 0>, POD2G_THREADS, 0);
         cudaGetLastError();
         if (occ > 0) {
-            c->rows_kernel |= 3;
+            c->rows_kernel |= 1;
             c->ws_occ = occ;
             c->grid_rows = std::max(CLUSTER, std::min(8 * c->num_sms, occ * c->num_sms) / CLUSTER * CLUSTER);
             c->grid_spmv = c->grid_rows;
