@@ -629,6 +629,9 @@ def gb300_arm(args):
                 extra["serving"]["workload"] = sx["workload"]
                 del vh, bh
             rx.close()
+        # the small 2D diffusion problem (3,969 unknowns): launch- and latency-bound
+        if not args.no_small:
+            extra["small_problem"] = small_problem_entry(pkg, args.tol)
         # CPU baseline: the oracle on the host cores, a bounded sample
         if not args.no_cpu:
             try:
@@ -669,6 +672,54 @@ def gb300_arm(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def small_problem_entry(pkg, tol):
+    """Q1 64 x 64 diffusion (3,969 unknowns, k = 10): the plain FP64 path on one query (host-checked
+    convergence every iteration), and the batched mixed path at batch 1 and 64 (CUDA graph of 8
+    iterations per launch): per-iteration times show the launch and latency cost of a problem this small."""
+    import torch
+    from synth.problems import Workload
+    from synth.snapshots import pod_basis
+    wl = Workload("q1_64")
+    P = wl.problem
+    Phi = pod_basis(wl)
+    out = {"workload": f"2D Poisson Q1 64x64, lognormal kappa: {P.n:,} dofs, k={wl.spec.k}, tol {fmt_tol(tol)}"}
+    xis, bs = wl.query_thetas(64), wl.rhs(64)
+    sp = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64, omega=wl.spec.omega, max_batch=1)
+    assert sp.set_values(0, wl.values(xis[0])) == pkg.OK
+    times, its = [], []
+    for r in range(6):
+        t0 = time.perf_counter()
+        _, it, _, st = sp.solve(0, bs[0], tol=tol, maxit=MAXIT)
+        times.append(time.perf_counter() - t0)
+        its.append(it)
+        assert st == pkg.OK
+    sp.close()
+    tm = statistics.median(times[1:])
+    out["plain_fp64"] = {"ms_per_solve": 1e3 * tm, "iters": int(its[-1]), "us_per_iteration": 1e6 * tm / its[-1]}
+    for B in (1, 64):
+        s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.MIXED_FP32PHI, omega=wl.spec.omega, max_batch=B)
+        vals = wl.values_torch(xis[:B], device="cuda").reshape(B, -1).contiguous()
+        b_dev = torch.from_numpy(bs[:B]).cuda()
+        x_dev = torch.empty_like(b_dev)
+        slots = list(range(B))
+        st, _ = s.set_values_batch_dev(slots, vals)
+        assert st == pkg.OK
+        for _ in range(2):
+            it, rel, sts, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=tol, maxit=MAXIT)
+        torch.cuda.synchronize()
+        reps = 5
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            it, rel, sts, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=tol, maxit=MAXIT)
+            assert rc == pkg.OK
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0) / reps
+        s.close()
+        out[f"batched_b{B}"] = {"ms_per_step": ms, "solves_per_s": B / (ms / 1e3), "iters_max": int(np.max(it)),
+                               "us_per_iteration": 1e3 * ms / int(np.max(it))}
+    return out
 
 
 def serving_entry(args, s, pkg, wl, vals_h, b_h, value):
@@ -906,6 +957,7 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "sgs"],
                     help="relaxation of the two-grid cycle: damped Jacobi or multicolour symmetric Gauss-Seidel")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-x0 comparison key")
+    ap.add_argument("--no-small", action="store_true", help="skip the small-problem (Q1 64x64) key")
     ap.add_argument("--x0", default="zero", choices=["zero", "rom", "sur"],
                     help="initial guess: zero, the POD reduced-order solution Phi K_c^-1 Phi^T b, or the "
                          "surrogate's prediction from the parameters")
