@@ -1275,7 +1275,8 @@ k_rows_v1(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
 }
 
 // ---------------------------------------------------------------------------- prolongation + post-smoothing from K Phi
-// With W = K Phi of each slot stored (FP32, [n][KP][Bp], formed at set-up with K_c), the product
+// With W = K Phi of each slot stored (FP32, mode-major [KP][n][Bp], so that a warp reads one mode of
+// consecutive unknowns and slots in one coalesced run; formed at set-up with K_c), the product
 // K y2 of the post-smoothing needs no pass over the matrix: y2 = y1 + Phi e_c, and
 // K y2 = K y1 + W e_c = (r - r1) + W e_c, since the pre-smoothing pass left r1 = r - K y1. Hence
 //     s = y2 + omega D^-1 (r - K y2) = y2 + omega D^-1 (r1 - W e_c),
@@ -1305,7 +1306,8 @@ k_postw(Dims D, int want, int pr, const float* __restrict__ dinv, const float2* 
              it += (long long)gridDim.x * blockDim.x) {
             const long long d = it >> D.lgBp;
             const float4* ph = reinterpret_cast<const float4*>(phi + d * KP);
-            const float* wr = W + d * KP * D.Bp + lane;
+            const float* wr = W + d * D.Bp + lane;   // W[m][d][slot]: mode m at wr + m * n * Bp
+            const long long mstride = n * D.Bp;
             const float2 rv = r[it];
             const float dv = dinv[it];
             const float r1v = r1[it];
@@ -1314,8 +1316,8 @@ k_postw(Dims D, int want, int pr, const float* __restrict__ dinv, const float2* 
 #pragma unroll
             for (int m4 = 0; m4 < KP / 4; ++m4) {
                 const float4 f = __ldg(ph + m4);
-                const float w0 = __ldg(wr + (4 * m4 + 0) * D.Bp), w1 = __ldg(wr + (4 * m4 + 1) * D.Bp);
-                const float w2 = __ldg(wr + (4 * m4 + 2) * D.Bp), w3 = __ldg(wr + (4 * m4 + 3) * D.Bp);
+                const float w0 = __ldg(wr + (4 * m4 + 0) * mstride), w1 = __ldg(wr + (4 * m4 + 1) * mstride);
+                const float w2 = __ldg(wr + (4 * m4 + 2) * mstride), w3 = __ldg(wr + (4 * m4 + 3) * mstride);
                 const float e0 = el[4 * m4], e1 = el[4 * m4 + 1], e2 = el[4 * m4 + 2], e3 = el[4 * m4 + 3];
                 y = __fmaf_rn(f.x, e0, y);
                 y2 = __fmaf_rn(f.y, e1, y2);

@@ -122,7 +122,7 @@ struct pod2g_ctx {
     double* d_b64 = nullptr;            // [n][Bp] the right-hand sides in FP64 (final residual)
     float* d_s32 = nullptr;             // [n][Bp]
     float* d_y32 = nullptr;             // [n][Bp]
-    float* d_W32 = nullptr;             // [n][kp][Bp] K Phi per slot (FP32), when the post-smoothing uses it
+    float* d_W32 = nullptr;             // [kp][n][Bp] K Phi per slot (FP32), when the post-smoothing uses it
     float* d_ec = nullptr;              // [Bp][kp] coarse corrections
     double* d_part = nullptr;           // reduction partials [G][Bp][2] (scalars)
     double* d_cpart = nullptr;          // restriction partials [G][Bp][kp]

@@ -134,12 +134,14 @@ __global__ void k_w_f64(const int32_t* __restrict__ row_ptr, const int32_t* __re
     W[d * kp + m] = acc;
 }
 
-// W = K Phi (double-float [n][kp]) -> the slot's lane of the FP32 copy [n][kp][Bp] used by the
-// post-smoothing pass that forms K y2 from it
-__global__ void k_w32(const float2* __restrict__ W, long long total, int Bp, int slot, float* __restrict__ W32) {
+// W = K Phi (double-float [n][kp]) -> the slot's lane of the FP32 copy, mode-major [kp][n][Bp], used by
+// the post-smoothing pass that forms K y2 from it (a thread per (mode, unknown), unknowns fastest)
+__global__ void k_w32(const float2* __restrict__ W, long long n, int kp, int Bp, int slot, float* __restrict__ W32) {
+    const long long total = n * kp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const float2 w = W[e];
+        const long long m = e / n, d = e - m * n;
+        const float2 w = W[d * kp + m];
         W32[e * Bp + slot] = __fadd_rn(w.x, w.y);
     }
 }
@@ -530,7 +532,7 @@ static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
         if (c->d_W32) {
             const long long tot = (long long)n * c->kp;
             k_w32<<<std::max(1, std::min(ceil_div(tot, T), 8 * c->num_sms)), T, 0, c->stream>>>(
-                (const float2*)c->d_W, tot, c->Bp, slot, c->d_W32);
+                (const float2*)c->d_W, (long long)n, c->kp, c->Bp, slot, c->d_W32);
             P2G_TRY(pod2g_check_launch(c));
         }
         if (c->coarse_tc) {
