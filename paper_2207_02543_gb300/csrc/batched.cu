@@ -2400,6 +2400,8 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
     const int row_f[NC] = {3, 4, 5, 6, 8}, res_f[NC] = {1, 2, 3, 4, 4}, vec_f[NC] = {2, 3, 4, 6, 8};
     pod2g_tuning cand[NC];
     for (int j = 0; j < NC; ++j) {
+        cand[j] = pod2g_tuning();
+        cand[j].restrict_rows = 0;
         cand[j].grid_rows = r8(row_f[j] * sms, need_rows);
         cand[j].grid_spmv = cand[j].grid_rows;
         cand[j].grid_restrict = r8(res_f[j] * sms, 4 * sms);
@@ -2453,7 +2455,7 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
         return b;
     };
     auto row_cand = [&](int j) -> const pod2g_tuning& { return j < NC ? cand[j] : cand_ws[j - NC]; };
-    pod2g_tuning pick;
+    pod2g_tuning pick = pod2g_tuning();
     const int br = best(t_rows, 2 * NC), bsp = best(t_spmv, 2 * NC);
     pick.grid_rows = row_cand(br).grid_rows;
     pick.grid_spmv = row_cand(bsp).grid_spmv;

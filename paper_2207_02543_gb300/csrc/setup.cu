@@ -135,14 +135,22 @@ __global__ void k_w_f64(const int32_t* __restrict__ row_ptr, const int32_t* __re
 }
 
 // W = K Phi (double-float [n][kp]) -> the slot's lane of the FP32 copy, mode-major [kp][n][Bp], used by
-// the post-smoothing pass that forms K y2 from it (a thread per (mode, unknown), unknowns fastest)
+// the post-smoothing pass that forms K y2 from it. A CTA transposes tiles of 64 unknowns through shared
+// memory: it reads their rows of W as one contiguous run and writes each mode's 64 entries together.
 __global__ void k_w32(const float2* __restrict__ W, long long n, int kp, int Bp, int slot, float* __restrict__ W32) {
-    const long long total = n * kp;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long m = e / n, d = e - m * n;
-        const float2 w = W[d * kp + m];
-        W32[e * Bp + slot] = __fadd_rn(w.x, w.y);
+    __shared__ float tile[64][POD2G_MAX_K + 1];
+    for (long long d0 = (long long)blockIdx.x * 64; d0 < n; d0 += (long long)gridDim.x * 64) {
+        const int rows = (int)min(64LL, n - d0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * kp; e += blockDim.x) {
+            const float2 w = W[d0 * kp + e];
+            tile[e / kp][e % kp] = __fadd_rn(w.x, w.y);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * kp; e += blockDim.x) {
+            const int m = e / rows, dd = e - m * rows;
+            W32[((long long)m * n + d0 + dd) * Bp + slot] = tile[dd][m];
+        }
     }
 }
 
@@ -530,8 +538,7 @@ static int setup_from_stage32(pod2g_ctx* c, int slot, int* st) {
                                                       c->bs, c->kp, (float2*)c->d_W);
         P2G_TRY(pod2g_check_launch(c));
         if (c->d_W32) {
-            const long long tot = (long long)n * c->kp;
-            k_w32<<<std::max(1, std::min(ceil_div(tot, T), 8 * c->num_sms)), T, 0, c->stream>>>(
+            k_w32<<<std::max(1, std::min(ceil_div(n, 64), 8 * c->num_sms)), T, 0, c->stream>>>(
                 (const float2*)c->d_W, (long long)n, c->kp, c->Bp, slot, c->d_W32);
             P2G_TRY(pod2g_check_launch(c));
         }

@@ -11,7 +11,7 @@ pod2g_autotune, pod2g_solve_batch_dev, tol 1e-8). Checks:
   * a sampled instance against the FP64 oracle run on the same rounded values and
     rounded basis: relative 2-norm error of x <= 1e-6 and iteration counts within +-2.
 The same checks run for the 3D Hex8 64^3 workload (823,875 unknowns, 32 instances, BF16 basis,
-k = 30). For the 3D Hex8 128^3 workload (6,440,067 unknowns, 57,066,625 blocks, 4 instances,
+k = 30) and the 2D diffusion Q1 1024^2 workload (1,046,529 unknowns, 16 instances, k = 25). For the 3D Hex8 128^3 workload (6,440,067 unknowns, 57,066,625 blocks, 4 instances,
 k = 40), where one oracle solve takes about a quarter of an hour on one core, the iteration
 counts are compared with the oracle's own stored counts (tests/golden/oracle_iterations.json,
 written by a script that runs only the oracle) within +-2, and every instance passes the FP64
@@ -108,6 +108,12 @@ def test_q4_512_batch64_full_size(pkg):
 def test_hex8_64_batch32_full_size(pkg):
     # 3D Hex8 elasticity 64^3 (823,875 unknowns, 3x3 BSR), k = 30 from 300 snapshots, BF16 basis, 32 instances
     _run_batch(pkg, "hex8_64", sample=[5])
+
+
+def test_q1_1024_batch16_full_size(pkg):
+    # 2D diffusion Q1 1024^2 (1,046,529 unknowns, scalar rows), k = 25 from 250 snapshots, 16 instances:
+    # the third problem of the serving mix
+    _run_batch(pkg, "q1_1024", sample=[3])
 
 
 def test_hex8_128_batch4_full_size(pkg):
