@@ -2097,7 +2097,11 @@ int batched_alloc(pod2g_ctx* c) {
         if (occ > 0) {
             c->rows_kernel |= 1;
             c->ws_occ = occ;
-            c->grid_rows = std::max(CLUSTER, std::min(8 * c->num_sms, occ * c->num_sms) / CLUSTER * CLUSTER);
+            // no more CTAs than rows to cover (a group of lanes per row, 256 / LPR rows per CTA)
+            const int lpr = c->bs == 3 ? 32 : 16;
+            const int need = ceil_div(c->nb, POD2G_THREADS / lpr);
+            c->grid_rows = std::max(CLUSTER, std::min(std::min(8 * c->num_sms, occ * c->num_sms),
+                                                      ceil_div(need, CLUSTER) * CLUSTER) / CLUSTER * CLUSTER);
             c->grid_spmv = c->grid_rows;
         }
     }
@@ -2117,7 +2121,11 @@ int batched_alloc(pod2g_ctx* c) {
             // fed as 8-CTA clusters retire)
             c->rows_kernel |= 3;
             c->ws_occ = occ;
-            c->grid_rows = std::max(CLUSTER, std::min(8 * c->num_sms, 4 * occ * c->num_sms) / CLUSTER * CLUSTER);
+            // no more CTAs than row groups to cover (8 warps of 32 / LR rows per CTA)
+            const int rpw = 32 / (c->Bp / ws_spt(c->Bp));
+            const int need = ceil_div(c->nb, (POD2G_THREADS / 32) * rpw);
+            c->grid_rows = std::max(CLUSTER, std::min(std::min(8 * c->num_sms, 4 * occ * c->num_sms),
+                                                      ceil_div(need, CLUSTER) * CLUSTER) / CLUSTER * CLUSTER);
             c->grid_spmv = c->grid_rows;
         }
     }
