@@ -676,8 +676,9 @@ def gb300_arm(args):
 
 def small_problem_entry(pkg, tol):
     """Q1 64 x 64 diffusion (3,969 unknowns, k = 10): the plain FP64 path on one query (host-checked
-    convergence every iteration), and the batched mixed path at batch 1 and 64 (CUDA graph of 8
-    iterations per launch): per-iteration times show the launch and latency cost of a problem this small."""
+    convergence every iteration), and the batched mixed path at batch 1 and 64, in its default form for a
+    problem this small (whole iterations in one persistent launch) and as a CUDA graph of 8 iterations
+    per launch: per-iteration times show the launch and latency cost of a problem this small."""
     import torch
     from synth.problems import Workload
     from synth.snapshots import pod_basis
@@ -698,7 +699,7 @@ def small_problem_entry(pkg, tol):
     sp.close()
     tm = statistics.median(times[1:])
     out["plain_fp64"] = {"ms_per_solve": 1e3 * tm, "iters": int(its[-1]), "us_per_iteration": 1e6 * tm / its[-1]}
-    for B in (1, 64):
+    for B, form in ((1, "persistent"), (64, "persistent"), (1, "graph"), (64, "graph")):
         s = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.MIXED_FP32PHI, omega=wl.spec.omega, max_batch=B)
         vals = wl.values_torch(xis[:B], device="cuda").reshape(B, -1).contiguous()
         b_dev = torch.from_numpy(bs[:B]).cuda()
@@ -706,6 +707,12 @@ def small_problem_entry(pkg, tol):
         slots = list(range(B))
         st, _ = s.set_values_batch_dev(slots, vals)
         assert st == pkg.OK
+        tune = s.get_tuning()
+        if form == "graph":
+            assert s.set_tuning(rows_kernel=tune["rows_kernel"] & 7) == pkg.OK
+        elif not tune["rows_kernel"] & 8:
+            s.close()
+            continue
         for _ in range(2):
             it, rel, sts, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=tol, maxit=MAXIT)
         torch.cuda.synchronize()
@@ -717,8 +724,11 @@ def small_problem_entry(pkg, tol):
         torch.cuda.synchronize()
         ms = 1e3 * (time.perf_counter() - t0) / reps
         s.close()
-        out[f"batched_b{B}"] = {"ms_per_step": ms, "solves_per_s": B / (ms / 1e3), "iters_max": int(np.max(it)),
-                               "us_per_iteration": 1e3 * ms / int(np.max(it))}
+        key = f"batched_b{B}" if form == "persistent" else f"batched_b{B}_graph"
+        out[key] = {"ms_per_step": ms, "solves_per_s": B / (ms / 1e3), "iters_max": int(np.max(it)),
+                    "us_per_iteration": 1e3 * ms / int(np.max(it)),
+                    "form": ("one persistent launch per 8 iterations" if form == "persistent" else
+                             "CUDA graph of 8 iterations x 7 kernels"), "grid_persist": tune["grid_persist"]}
     return out
 
 

@@ -376,10 +376,17 @@ typedef struct {
                                at set-up, without a sweep over the matrix (contexts that store K Phi:
                                assembled, Jacobi with r1 = r2 = 1, K Phi smaller than the values and
                                within the HBM budget). 0 = one thread per block row and slot, and the
-                               post-smoothing as a sweep. Default: every form the context supports. */
+                               post-smoothing as a sweep. Bit 3: whole iterations run in one
+                               cooperative launch of grid_persist CTAs with grid-wide barriers between
+                               the phases (assembled, Jacobi with r1 = r2 = 1, at most 64 slot lanes,
+                               K Phi stored or no coarse space); default where n * lanes <= 2^20, for
+                               which the eight launches per iteration of the graph path cost more than
+                               their work. Default: every other form the context supports. */
     int32_t restrict_rows;  /* rows of Phi and r1 per shared-memory chunk of the bulk-staged
                                restriction (its tile; multiple of 4, 4..256, within 200 KB of shared
                                memory; 4 or more slot lanes); 0 = the default (~24 KB per chunk) */
+    int32_t grid_persist;   /* CTAs of the persistent launch (rows_kernel bit 3): 1..the number that
+                               fit on the GPU at once, at most 4*SMs; 0 where the form does not apply */
 } pod2g_tuning;
 
 /* Current shape (mixed contexts; FP64 contexts return POD2G_INVALID_ARG). */
@@ -387,7 +394,9 @@ int pod2g_get_tuning(pod2g_t ctx, pod2g_tuning* out);
 /* Set a shape; POD2G_INVALID_ARG if a field is out of range or the context is serving. */
 int pod2g_set_tuning(pod2g_t ctx, const pod2g_tuning* t);
 /* Autotuner: for five candidate shapes (and, where they apply, five grid sizes of the
- * warp-staged row kernels, then half and twice the restriction's default chunk), solve the given set-up slots with right-hand
+ * warp-staged row kernels, then half and twice the restriction's default chunk, then the
+ * persistent launch at up to four grid sizes against the graph of the chosen shape, timed
+ * per launch), solve the given set-up slots with right-hand
  * sides b_dev (nslots consecutive vectors of n doubles, device) for `iters`
  * iterations (rounded up to whole graph launches), timing each kernel with CUDA
  * events, and keep per kernel group the fastest candidate (kernel form and grid). The slots are left idle

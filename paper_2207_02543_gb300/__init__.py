@@ -48,7 +48,7 @@ class Elements(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("grid_rows", C.c_int32), ("grid_restrict", C.c_int32), ("grid_prol", C.c_int32),
                 ("grid_vec", C.c_int32), ("grid_spmv", C.c_int32), ("rows_kernel", C.c_int32),
-                ("restrict_rows", C.c_int32)]
+                ("restrict_rows", C.c_int32), ("grid_persist", C.c_int32)]
 
 
 class Opts(C.Structure):

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpod2g.so")
-SOURCES = ["api.cu", "setup.cu", "plain.cu", "batched.cu", "serve.cu", "noalloc.cu", "rom.cu", "surrogate.cu"]
+SOURCES = ["api.cu", "setup.cu", "plain.cu", "batched.cu", "serve.cu", "noalloc.cu", "rom.cu", "surrogate.cu", "persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xptxas", "-O3",
          "-DNDEBUG"]

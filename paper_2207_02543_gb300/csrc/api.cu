@@ -365,10 +365,11 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
         ALLOC(c->d_b64, sizeof(double) * n * Bp);
         ALLOC(c->d_s32, sizeof(float) * n * Bp);
         ALLOC(c->d_y32, sizeof(float) * n * Bp);
-        // K Phi per slot, for the post-smoothing without a matrix sweep (k_postw), when it is smaller
-        // than the slot's matrix values and fits the budget; otherwise the context does without it
+        // K Phi per slot, for the post-smoothing without a matrix sweep (k_postw and the persistent
+        // launch), when it is smaller than the slot's matrix values or the problem is small enough for
+        // the persistent launch, and it fits the budget; otherwise the context does without it
         if (!c->elem && c->smoother == POD2G_SMOOTHER_JACOBI && c->pre == 1 && c->post == 1 && kp > 0 &&
-            (long long)n * kp < tot) {
+            ((long long)n * kp < tot || (long long)n * Bp <= POD2G_PERSIST_ITEMS)) {
             if (dev_alloc(c, (void**)&c->d_W32, sizeof(float) * n * kp * Bp) != POD2G_OK) c->d_W32 = nullptr;
         }
         ALLOC(c->d_ec, sizeof(float) * std::max(1, Bp * kp));
@@ -509,6 +510,7 @@ int pod2g_get_tuning(pod2g_t c, pod2g_tuning* out) {
     out->grid_spmv = c->grid_spmv;
     out->rows_kernel = c->rows_kernel;
     out->restrict_rows = c->restrict_rows;
+    out->grid_persist = c->grid_persist;
     return POD2G_OK;
 }
 

@@ -37,6 +37,7 @@
 //   k_prol   y2 = y1 + Phi e_c
 //   k_post   s = y2 + omega D^-1 (r - K y2), r^T s  (last cluster: beta)
 #include "common.cuh"
+#include "lanes.cuh"
 
 #include <cooperative_groups.h>
 
@@ -83,36 +84,6 @@ struct Dims {
     double omega;
 };
 
-// p[g0*stride] + ... + p[(g1-1)*stride], added in increasing g (so the result is
-// that of the plain serial loop); loads are issued eight at a time.
-__device__ __forceinline__ double ordered_sum(const double* __restrict__ p, int g0, int g1, long long stride) {
-    double s = 0.0;
-    int g = g0;
-    for (; g + 8 <= g1; g += 8) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = p[(long long)(g + u) * stride];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s += v[u];
-    }
-    for (; g < g1; ++g) s += p[(long long)g * stride];
-    return s;
-}
-
-// Per-slot CTA sum: thread t contributes v to slot t % Bp; the sums (in thread
-// order) land in s_out[slot]. Ends with a barrier.
-__device__ __forceinline__ void cta_lane_sum(double v, int Bp, double* s_tmp, double* s_out) {
-    __syncthreads();
-    s_tmp[threadIdx.x] = v;
-    __syncthreads();
-    if ((int)threadIdx.x < Bp) {
-        double s = 0.0;
-        for (int t = threadIdx.x; t < (int)blockDim.x; t += Bp) s += s_tmp[t];
-        s_out[threadIdx.x] = s;
-    }
-    __syncthreads();
-}
-
 // The cluster's rank-0 CTA sums s_vals[0..nv) of all CTAs of its cluster (rank
 // order, read through distributed shared memory) into out[0..nv).
 __device__ __forceinline__ void cluster_store(const double* s_vals, int nv, double* out) {
@@ -145,25 +116,6 @@ __device__ __forceinline__ bool last_cluster_arrive(unsigned* counter, int nclus
     if (am_last) __threadfence();
     return am_last;
 }
-
-// total over partial rows g = 0..NP-1 of part[g * stride + slot] (fixed order),
-// computed by all threads of one CTA; the total is returned in threads t < Bp.
-__device__ __forceinline__ double grid_lane_total(const double* part, int NP, int stride, int Bp, double* s_tmp) {
-    const int Q = blockDim.x / Bp;
-    const int b = threadIdx.x % Bp, q = threadIdx.x / Bp;
-    const int g0 = (int)((long long)NP * q / Q), g1 = (int)((long long)NP * (q + 1) / Q);
-    double s = ordered_sum(part + b, g0, g1, stride);
-    __syncthreads();
-    s_tmp[threadIdx.x] = s;
-    __syncthreads();
-    double tot = 0.0;
-    if ((int)threadIdx.x < Bp)
-        for (int qq = 0; qq < Q; ++qq) tot += s_tmp[qq * Bp + threadIdx.x];
-    return tot;
-}
-
-__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 df_of(float a) { return make_float2(a, 0.f); }
 
 // Prefetching loop over the blocks b0..b1 of one block row: for each group of
 // UNROLL blocks, `fetch_blk(u, blk)` issues the loads that depend only on the block
@@ -2129,6 +2081,13 @@ int batched_alloc(pod2g_ctx* c) {
             c->grid_spmv = c->grid_rows;
         }
     }
+    // whole iterations in one launch: as many CTAs as the rows need (256 row-slot items each),
+    // all resident at once; the default for problems small enough to be launch-bound
+    const int pmax = std::min(persist_max_grid(c), 4 * c->num_sms);
+    if (pmax > 0) {
+        c->grid_persist = std::max(1, std::min(pmax, ceil_div((long long)c->nb * c->Bp, POD2G_THREADS)));
+        if ((long long)c->n * c->Bp <= POD2G_PERSIST_ITEMS) c->rows_kernel |= 8;
+    }
     if (c->precision != POD2G_FP64 && c->kp > 0) {
         const int sm_r = (int)(restrict_bulk_smem(c) ? restrict_bulk_smem(c) : restrict_smem(c->Bp, c->kp));
         const int lb = restrict_lb(c->Bp, c->kp);
@@ -2230,12 +2189,29 @@ static int build_graph(pod2g_ctx* c) {
     return POD2G_OK;
 }
 
-// One CUDA-graph launch (`chunk` PCG iterations for the ACTIVE lanes), then the
-// per-slot scalars are copied back to the host mirror.
-int batched_chunk(pod2g_ctx* c) {
+// Whole iterations in one cooperative launch (rows_kernel bit 3; not in per-kernel timing mode).
+static bool persist_on(const pod2g_ctx* c) {
+    return (c->rows_kernel & 8) && !c->timing && c->grid_persist > 0 && persist_applies(c);
+}
+
+// `chunk` PCG iterations for the ACTIVE lanes: one persistent launch, or one replay of
+// the captured graph.
+static int launch_iterations(pod2g_ctx* c) {
+    if (persist_on(c)) {
+        P2G_TRY(persist_launch(c, c->chunk));
+        c->launches += 1;
+        return POD2G_OK;
+    }
     P2G_TRY(build_graph(c));
     P2G_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
     c->launches += c->iter_launches * c->chunk;
+    return POD2G_OK;
+}
+
+// One launch of `chunk` PCG iterations for the ACTIVE lanes, then the per-slot
+// scalars are copied back to the host mirror.
+int batched_chunk(pod2g_ctx* c) {
+    P2G_TRY(launch_iterations(c));
     P2G_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     P2G_CUDA(cudaStreamSynchronize(c->stream));
@@ -2291,9 +2267,7 @@ int batched_run(pod2g_ctx* c, const std::vector<int>& lanes) {
     SlotScalars* hb[2] = {c->h_sc, c->h_sc2};
     int* he[2] = {c->h_err, c->h_err2};
     auto enqueue = [&](int64_t k) -> int {
-        P2G_TRY(build_graph(c));
-        P2G_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
-        c->launches += c->iter_launches * c->chunk;
+        P2G_TRY(launch_iterations(c));
         P2G_CUDA(cudaMemcpyAsync(hb[k & 1], c->d_sc, sizeof(SlotScalars) * c->Bp, cudaMemcpyDeviceToHost, c->stream));
         P2G_CUDA(cudaMemcpyAsync(he[k & 1], c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         P2G_CUDA(cudaEventRecord(c->la_ev[k & 1], c->stream));
@@ -2367,9 +2341,12 @@ int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
     if (t->grid_spmv < CLUSTER || t->grid_spmv % CLUSTER || t->grid_spmv > 8 * sms) return POD2G_INVALID_ARG;
     if (t->grid_restrict < CLUSTER || t->grid_restrict % CLUSTER || t->grid_restrict > 4 * sms) return POD2G_INVALID_ARG;
     if (t->grid_prol < 1 || t->grid_prol > 8 * sms || t->grid_vec < 1 || t->grid_vec > 8 * sms) return POD2G_INVALID_ARG;
-    if (t->rows_kernel < 0 || t->rows_kernel > 7 ||
+    if (t->rows_kernel < 0 || t->rows_kernel > 15 ||
         ((t->rows_kernel & 3) && !((ws_applies(c) || v1_applies(c)) && c->ws_occ > 0)) ||
         ((t->rows_kernel & 4) && !c->d_W32))
+        return POD2G_INVALID_ARG;
+    const int pmax = std::min(persist_max_grid(c), 4 * sms);
+    if (t->grid_persist < 0 || t->grid_persist > pmax || ((t->rows_kernel & 8) && t->grid_persist < 1))
         return POD2G_INVALID_ARG;
     if (t->restrict_rows != 0 &&
         (t->restrict_rows < 4 || t->restrict_rows > 256 || t->restrict_rows % 4 || c->Bp < 4 || c->kp == 0 ||
@@ -2381,6 +2358,7 @@ int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t) {
         return POD2G_INVALID_ARG;
     c->restrict_rows = t->restrict_rows;
     c->rows_kernel = t->rows_kernel;
+    if (t->grid_persist > 0) c->grid_persist = t->grid_persist;
     c->grid_rows = t->grid_rows;
     c->grid_spmv = t->grid_spmv;
     c->grid_restrict = t->grid_restrict;
@@ -2422,8 +2400,10 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
     const int ws_f[NC] = {1, 2, 3, 4, 8};
     pod2g_tuning cand_ws[NC];
     const int kbit = c->rows_kernel & 4;   // the K Phi form of the post-smoothing is kept as set
+    const int gpers = c->grid_persist;
     for (int j = 0; j < NC; ++j) {
         cand[j].rows_kernel = kbit;
+        cand[j].grid_persist = gpers;
         cand_ws[j] = cand[j];
         cand_ws[j].rows_kernel = 3 | kbit;
         cand_ws[j].grid_rows = r8(ws_f[j] * wave, 8 * sms);
@@ -2491,6 +2471,55 @@ int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b
                 pick.restrict_rows = R;
             }
         }
+    }
+    // whole launches: the graph of the chosen shape against the persistent launch at up to
+    // four grid sizes (the rows' need, one and two CTAs per SM, every resident CTA), each timed
+    // over `iters` iterations with CUDA events around the launches
+    const int pmax = std::min(persist_max_grid(c), 4 * sms);
+    pick.grid_persist = pmax > 0 ? c->grid_persist : 0;
+    if (pmax > 0) {
+        cudaEvent_t e0, e1;
+        P2G_CUDA(cudaEventCreate(&e0));
+        P2G_CUDA(cudaEventCreate(&e1));
+        auto per_iter = [&](const pod2g_tuning& t, double* ms) -> int {
+            P2G_TRY(batched_set_tuning(c, &t));
+            P2G_TRY(batched_set_timing(c, 0));
+            P2G_TRY(batched_load(c, nslots, slots, b_dev, nullptr, tol.data(), maxit.data()));
+            P2G_TRY(batched_chunk(c));  // warm-up (graph instantiation)
+            P2G_CUDA(cudaEventRecord(e0, c->stream));
+            int n_it = 0;
+            for (int it = 0; it < iters; it += c->chunk, n_it += c->chunk) P2G_TRY(batched_chunk(c));
+            P2G_CUDA(cudaEventRecord(e1, c->stream));
+            P2G_CUDA(cudaEventSynchronize(e1));
+            float f = 0.f;
+            P2G_CUDA(cudaEventElapsedTime(&f, e0, e1));
+            *ms = (double)f / std::max(1, n_it);
+            return POD2G_OK;
+        };
+        int st = POD2G_OK;
+        double t_best = 1e300;
+        pod2g_tuning tg = pick;
+        tg.rows_kernel &= 7;
+        st = per_iter(tg, &t_best);
+        const int need = std::max(1, ceil_div((long long)c->nb * c->Bp, POD2G_THREADS));
+        const int gp[4] = {std::min(need, pmax), std::min(sms, pmax), std::min(2 * sms, pmax), pmax};
+        for (int j = 0; j < 4 && st == POD2G_OK; ++j) {
+            bool seen = false;
+            for (int i = 0; i < j; ++i) seen |= gp[i] == gp[j];
+            if (seen) continue;
+            pod2g_tuning tp = tg;
+            tp.rows_kernel |= 8;
+            tp.grid_persist = gp[j];
+            double ms = 1e300;
+            st = per_iter(tp, &ms);
+            if (st == POD2G_OK && ms < t_best) {
+                t_best = ms;
+                pick = tp;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        P2G_TRY(st);
     }
     P2G_TRY(batched_set_tuning(c, &pick));
     P2G_TRY(batched_set_timing(c, timing0 ? 1 : 0));

@@ -22,6 +22,7 @@
 #define POD2G_MAX_BP 256       // largest slot-lane count
 #define POD2G_ELEM_RE 8        // element positions per block row (elements adjacent to one node)
 #define POD2G_KREF_MAX 576     // reference-matrix entries, (npe * bs)^2 with npe * bs <= 24
+#define POD2G_PERSIST_ITEMS (1LL << 20)  // unknowns x slot lanes up to which whole iterations run in one launch by default
 
 // ---------------------------------------------------------------------------- slot states
 enum SlotState : int { SLOT_IDLE = 0, SLOT_JOINING = 1, SLOT_ACTIVE = 2, SLOT_DONE = 3 };
@@ -144,6 +145,7 @@ struct pod2g_ctx {
     int rows_kernel = 0;                // bit 0: staged smoother row kernels, bit 1: staged outer SpMV
     int ws_occ = 0;                     // resident CTAs per SM of the staged row kernels (0: not available)
     int restrict_rows = 0;              // rows per staged chunk of the restriction (0: default)
+    int grid_persist = 0;               // CTAs of the persistent launch (rows_kernel bit 3)
     cudaGraphExec_t graph_exec = nullptr;
     // per-kernel timing (event-record nodes around each kernel of the captured iterations)
     bool timing = false;
@@ -339,7 +341,7 @@ __device__ __forceinline__ void elem_block_values(uint64_t d, const float* ce, c
 }
 
 // counters used by the last-CTA reductions (indices into ctx->d_counters)
-enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT_W = 5, CNT_N = 16 };
+enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT_W = 5, CNT_PERSIST = 6, CNT_N = 16 };
 
 // ---------------------------------------------------------------------------- internal entry points
 int plain_solve(pod2g_ctx* c, int slot, const double* b_dev, const double* x0_dev, double tol, int maxit,
@@ -373,5 +375,9 @@ int batched_alloc(pod2g_ctx* c);
 int rom_solution(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, double* x_dev);
 int batched_set_tuning(pod2g_ctx* c, const pod2g_tuning* t);
 int batched_autotune(pod2g_ctx* c, int nslots, const int* slots, const double* b_dev, int iters);
+// persistent launch of whole iterations (persist.cu)
+bool persist_applies(const pod2g_ctx* c);
+int persist_max_grid(pod2g_ctx* c);
+int persist_launch(pod2g_ctx* c, int iters);
 void batched_free(pod2g_ctx* c);
 int dev_alloc(pod2g_ctx* c, void** p, size_t bytes);

@@ -93,7 +93,7 @@ def test_invalid_shapes_rejected(pkg):
     assert s.set_tuning(grid_spmv=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_restrict=0) == pkg.INVALID_ARG
     assert s.set_tuning(grid_vec=10 ** 6) == pkg.INVALID_ARG
-    assert s.set_tuning(rows_kernel=8) == pkg.INVALID_ARG
+    assert s.set_tuning(rows_kernel=16) == pkg.INVALID_ARG
     assert s.set_tuning(restrict_rows=6) == pkg.INVALID_ARG       # not a multiple of 4
     s.close()
     f = pkg.Solver(P.row_ptr, P.col_idx, P.bs, Phi, precision=pkg.FP64)
