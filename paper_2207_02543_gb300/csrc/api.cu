@@ -373,7 +373,7 @@ static int create_impl(const pod2g_pattern* pat, const pod2g_elements* el, const
             if (dev_alloc(c, (void**)&c->d_W32, sizeof(float) * n * kp * Bp) != POD2G_OK) c->d_W32 = nullptr;
         }
         ALLOC(c->d_ec, sizeof(float) * std::max(1, Bp * kp));
-        ALLOC(c->d_part, sizeof(double) * Gmax * Bp * 2);
+        ALLOC(c->d_part, sizeof(double) * (Gmax + 1) * Bp * 2);   // + the persistent launch's totals
         ALLOC(c->d_cpart, sizeof(double) * (size_t)Gmax * Bp * std::max(1, kp));
         ALLOC(c->d_sc, sizeof(SlotScalars) * Bp);
         ALLOC(c->d_mask, sizeof(int) * 2 * Bp);

@@ -1372,7 +1372,7 @@ struct WsCur {
 // KIND 2: s = y2 + omega D^-1 (r - K y2), partial r^T s (and r^T s_old), last cluster
 //         beta (as k_post with POST = 1).
 template <int BS, int SPT, int KIND>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, 2)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS, (BS == 3 && SPT == 2) ? 1 : 2)
 k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
           const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ vin,
           const float* __restrict__ yin, float2* __restrict__ qout, float* __restrict__ out, double* part,
@@ -1493,6 +1493,7 @@ k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
     load_cols(Gs, cjn);
     // accumulators of the lane's row and its own-row operands (loaded at the group's first chunk)
     float ah[BS][SPT], al[BS][SPT];
+    float bh[BS], bl[BS];      // KIND 0, one slot per lane, bs >= 2: the accumulators of the second column
     float2 own2[BS][SPT];      // KIND 0: p; KIND 1, 2: r
     float owny[BS][SPT], ownd[BS][SPT], owns[BS][SPT];
     bool bad = false;
@@ -1510,6 +1511,8 @@ k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
             for (int a = 0; a < BS; ++a)
 #pragma unroll
                 for (int s = 0; s < SPT; ++s) { ah[a][s] = 0.f; al[a][s] = 0.f; }
+#pragma unroll
+            for (int a = 0; a < BS; ++a) { bh[a] = 0.f; bl[a] = 0.f; }
             const int i = C.g * RPW + r;
             if (i < D.nb) {
 #pragma unroll
@@ -1531,6 +1534,44 @@ k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (cj[u] < 0) continue;
+            if constexpr (KIND == 0 && SPT == 2 && BS >= 2) {
+                // the lane's two slots in packed instructions (each accumulator sees the same
+                // operations in the same order as below)
+#pragma unroll
+                for (int cc = 0; cc < BS; ++cc) {
+                    const float2 h2 = make_float2(G[u][cc][0].x, G[u][cc][1].x);
+                    const float2 l2 = make_float2(G[u][cc][0].y, G[u][cc][1].y);
+                    const float2 nh2 = f2_mul(h2, make_float2(-1.f, -1.f));
+#pragma unroll
+                    for (int a = 0; a < BS; ++a) {
+                        float v[2];
+                        ws_ld1<2>(vb + (u * BB + a * BS + cc) * Bp, v);
+                        float2 hi = make_float2(ah[a][0], ah[a][1]), lo = make_float2(al[a][0], al[a][1]);
+                        df_acc_fma2(hi, lo, make_float2(v[0], v[1]), h2, nh2, l2);
+                        ah[a][0] = hi.x; ah[a][1] = hi.y;
+                        al[a][0] = lo.x; al[a][1] = lo.y;
+                    }
+                }
+                continue;
+            }
+            if constexpr (KIND == 0 && SPT == 1 && BS >= 2) {
+                // columns 0 and 1 of the block in packed instructions, into two accumulators per
+                // row (column 2 of a 3x3 block goes to the first, scalar); the two are added in
+                // double-float at the end of the row
+                const float2 h2 = make_float2(G[u][0][0].x, G[u][1][0].x);
+                const float2 l2 = make_float2(G[u][0][0].y, G[u][1][0].y);
+                const float2 nh2 = f2_mul(h2, make_float2(-1.f, -1.f));
+#pragma unroll
+                for (int a = 0; a < BS; ++a) {
+                    const float* va = vb + (u * BB + a * BS) * Bp;
+                    float2 hi = make_float2(ah[a][0], bh[a]), lo = make_float2(al[a][0], bl[a]);
+                    df_acc_fma2(hi, lo, make_float2(va[0], va[Bp]), h2, nh2, l2);
+                    ah[a][0] = hi.x; bh[a] = hi.y;
+                    al[a][0] = lo.x; bl[a] = lo.y;
+                    if constexpr (BS == 3) df_acc_fma(ah[a][0], al[a][0], va[2 * Bp], G[u][2][0].x, G[u][2][0].y);
+                }
+                continue;
+            }
 #pragma unroll
             for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -1556,7 +1597,10 @@ k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
                         float2 qv[SPT];
 #pragma unroll
                         for (int s = 0; s < SPT; ++s) {
-                            qv[s] = df_norm(ah[a][s], al[a][s]);
+                            if constexpr (SPT == 1 && BS >= 2)
+                                qv[s] = df_add(df_norm(ah[a][s], al[a][s]), df_norm(bh[a], bl[a]));
+                            else
+                                qv[s] = df_norm(ah[a][s], al[a][s]);
                             if (on[s]) {
                                 const float2 pv = own2[a][s];
                                 df_acc_fma(d1h[s], d1l[s], pv.x, qv[s].x, qv[s].y);
@@ -1856,14 +1900,15 @@ static void launch_post(pod2g_ctx* c, Dims D, int want) {
 }
 
 // ---- warp-staged row kernels (k_rows_ws): applicability, shared memory, launch
-static int ws_spt(int Bp) { return Bp > 32 ? Bp / 32 : 1; }
+// slots per lane: two above 32 slot lanes (a warp covers at most 32 lanes of a row)
+static int ws_spt(const pod2g_ctx* c) { return c->Bp > 32 ? 2 : 1; }
 // the staged kernels apply to assembled operators with 4 <= Bp <= 64 and Jacobi relaxation
 static bool ws_applies(const pod2g_ctx* c) {
     return !c->elem && c->precision != POD2G_FP64 && c->Bp >= 4 && c->Bp <= 64 &&
            c->smoother == POD2G_SMOOTHER_JACOBI;
 }
-static size_t ws_smem(int bs, int Bp) {
-    const int spt = ws_spt(Bp), rpw = 32 / (Bp / spt);
+static size_t ws_smem(int bs, int Bp, int spt) {
+    const int rpw = 32 / (Bp / spt);
     return (size_t)(POD2G_THREADS / 32) * WS_STAGES * ((size_t)rpw * ws_row_stride(bs, Bp, spt) * 4 + 8);
 }
 static bool ws_spmv(const pod2g_ctx* c) { return ws_applies(c) && (c->rows_kernel & 2); }
@@ -1898,7 +1943,7 @@ static void launch_post_v1(pod2g_ctx* c, Dims D, int want) {
 
 #define WS_DISPATCH(KIND, ...)                                                            \
     do {                                                                                   \
-        const bool two_ = ws_spt(c->Bp) == 2;                                              \
+        const bool two_ = ws_spt(c) == 2;                                                   \
         if (c->bs == 1) {                                                                  \
             if (two_) k_rows_ws<1, 2, KIND> __VA_ARGS__;                                   \
             else k_rows_ws<1, 1, KIND> __VA_ARGS__;                                        \
@@ -1912,19 +1957,19 @@ static void launch_post_v1(pod2g_ctx* c, Dims D, int want) {
     } while (0)
 
 static void launch_spmv_ws(pod2g_ctx* c, Dims D, int want) {
-    const size_t sm = ws_smem(c->bs, c->Bp);
+    const size_t sm = ws_smem(c->bs, c->Bp, ws_spt(c));
     WS_DISPATCH(0, <<<c->grid_spmv, POD2G_THREADS, sm, c->stream>>>(
                        D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_pdf, nullptr,
                        c->d_qdf, nullptr, c->d_part, c->d_counters + CNT_SPMV, c->d_sc, c->d_err));
 }
 static void launch_smooth1_ws(pod2g_ctx* c, Dims D, int want) {
-    const size_t sm = ws_smem(c->bs, c->Bp);
+    const size_t sm = ws_smem(c->bs, c->Bp, ws_spt(c));
     WS_DISPATCH(1, <<<D.G, POD2G_THREADS, sm, c->stream>>>(
                        D, want, 0, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_rdf, nullptr,
                        nullptr, c->d_y32, c->d_part, nullptr, c->d_sc, c->d_err));
 }
 static void launch_post_ws(pod2g_ctx* c, Dims D, int want) {
-    const size_t sm = ws_smem(c->bs, c->Bp);
+    const size_t sm = ws_smem(c->bs, c->Bp, ws_spt(c));
     WS_DISPATCH(2, <<<D.G, POD2G_THREADS, sm, c->stream>>>(
                        D, want, c->beta_pr, c->d_row_ptr, c->d_col_idx, c->d_vals32, c->d_dinv32, c->d_rdf,
                        c->d_y32, nullptr, c->d_s32, c->d_part, c->d_counters + CNT_POST, c->d_sc, c->d_err));
@@ -1932,7 +1977,7 @@ static void launch_post_ws(pod2g_ctx* c, Dims D, int want) {
 static int ws_set_attributes(pod2g_ctx* c) {
     const void* fns[3] = {nullptr, nullptr, nullptr};
 #define WS_FN(BS_, SPT_)                                                   \
-    if (c->bs == BS_ && ws_spt(c->Bp) == SPT_) {                           \
+    if (c->bs == BS_ && ws_spt(c) == SPT_) {                               \
         fns[0] = (const void*)k_rows_ws<BS_, SPT_, 0>;                     \
         fns[1] = (const void*)k_rows_ws<BS_, SPT_, 1>;                     \
         fns[2] = (const void*)k_rows_ws<BS_, SPT_, 2>;                     \
@@ -2061,9 +2106,9 @@ int batched_alloc(pod2g_ctx* c) {
         // staged row kernels by default: one wave of resident CTAs for the row kernels
         P2G_TRY(ws_set_attributes(c));
         int occ = 0;
-        const int sm = (int)ws_smem(c->bs, c->Bp);
+        const int sm = (int)ws_smem(c->bs, c->Bp, ws_spt(c));
 #define WS_OCC(BS_, SPT_)                                                                                   \
-        if (c->bs == BS_ && ws_spt(c->Bp) == SPT_)                                                          \
+        if (c->bs == BS_ && ws_spt(c) == SPT_)                                                              \
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_ws<BS_, SPT_, 0>, POD2G_THREADS, sm);
         WS_OCC(1, 1) WS_OCC(1, 2) WS_OCC(2, 1) WS_OCC(2, 2) WS_OCC(3, 1) WS_OCC(3, 2)
 #undef WS_OCC
@@ -2074,7 +2119,7 @@ int batched_alloc(pod2g_ctx* c) {
             c->rows_kernel |= 3;
             c->ws_occ = occ;
             // no more CTAs than row groups to cover (8 warps of 32 / LR rows per CTA)
-            const int rpw = 32 / (c->Bp / ws_spt(c->Bp));
+            const int rpw = 32 / (c->Bp / ws_spt(c));
             const int need = ceil_div(c->nb, (POD2G_THREADS / 32) * rpw);
             c->grid_rows = std::max(CLUSTER, std::min(std::min(8 * c->num_sms, 4 * occ * c->num_sms),
                                                       ceil_div(need, CLUSTER) * CLUSTER) / CLUSTER * CLUSTER);

@@ -257,6 +257,53 @@ __device__ __forceinline__ void df_acc_fma(float& hi, float& lo, float v, float 
     lo = __fadd_rn(lo, __fadd_rn(e, pe));
     lo = __fmaf_rn(v, pl, lo);
 }
+// ---- packed FP32 pairs: the f32x2 instructions of the sm_100 family apply one FP32 operation
+// (IEEE, round to nearest even, no flush to zero) to both halves of a 64-bit register pair,
+// in one instruction; each half is rounded exactly as the scalar operation rounds it.
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_of(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_of(d);
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_of(d);
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_of(d);
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+    return f2_of(d);
+}
+// df_acc_fma on two accumulators at once, in packed instructions: (hi.x, lo.x) += v.x (ph.x + pl.x)
+// and (hi.y, lo.y) += v.y (ph.y + pl.y), every operation rounded as in df_acc_fma (the sign
+// flips are exact: -(v ph) is formed as v (-ph), and p - bb as -((-p) + bb)). nph = -ph.
+__device__ __forceinline__ void df_acc_fma2(float2& hi, float2& lo, float2 v, float2 ph, float2 nph, float2 pl) {
+    const float2 np = f2_mul(v, nph);      // -p, p = v ph rounded
+    const float2 pe = f2_fma(v, ph, np);   // v ph - p, exact
+    const float2 s = f2_sub(hi, np);       // TwoSum(hi, p)
+    const float2 bb = f2_sub(s, hi);
+    const float2 t2 = f2_sub(hi, f2_sub(s, bb));
+    const float2 e = f2_sub(t2, f2_add(np, bb));
+    hi = s;
+    lo = f2_add(lo, f2_add(e, pe));
+    lo = f2_fma(v, pl, lo);
+}
 __device__ __forceinline__ float2 df_from_double(double d) {
     float hi = __double2float_rn(d);
     float lo = __double2float_rn(d - (double)hi);
@@ -341,7 +388,7 @@ __device__ __forceinline__ void elem_block_values(uint64_t d, const float* ce, c
 }
 
 // counters used by the last-CTA reductions (indices into ctx->d_counters)
-enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT_W = 5, CNT_PERSIST = 6, CNT_N = 16 };
+enum { CNT_SPMV = 0, CNT_POST = 1, CNT_RESID = 2, CNT_PLAIN = 3, CNT_AC = 4, CNT_W = 5, CNT_PERSIST = 6 /* and 7 */, CNT_N = 16 };
 
 // ---------------------------------------------------------------------------- internal entry points
 int plain_solve(pod2g_ctx* c, int slot, const double* b_dev, const double* x0_dev, double tol, int maxit,

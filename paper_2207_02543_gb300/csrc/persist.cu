@@ -51,11 +51,37 @@ struct PersistArgs {
     float* r1;
     float* ec;           // [Bp][kp]
     double* part;        // [G][2 Bp]
+    double* tot;         // [2 Bp] per-slot totals of part, written by the last CTA to arrive
     double* cpart;       // [G][Bp][kp]
     SlotScalars* sc;
-    unsigned* bar;       // arrivals, zero at launch
+    unsigned* bar;       // bar[0] arrivals, bar[1] the latest released summing barrier; zero at launch
     int* err;
 };
+
+// Per-slot total over the G partial rows part[g * 2 Bp + off + slot], in the same fixed
+// order in every CTA; returned in threads t < Bp.
+__device__ __forceinline__ double slot_total(const double* part, int G, int Bp, int off, double* s_tmp) {
+    const int Q = blockDim.x / Bp;
+    const int b = threadIdx.x % Bp, qd = threadIdx.x / Bp;
+    const int g0 = (int)((long long)G * qd / Q), g1 = (int)((long long)G * (qd + 1) / Q);
+    double s = 0.0;
+    int g = g0;
+    for (; g + 8 <= g1; g += 8) {   // eight loads in flight, added in order
+        double v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ldcg(part + (long long)(g + j) * 2 * Bp + off + b);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += v[j];
+    }
+    for (; g < g1; ++g) s += __ldcg(part + (long long)g * 2 * Bp + off + b);
+    __syncthreads();
+    s_tmp[threadIdx.x] = s;
+    __syncthreads();
+    double tot = 0.0;
+    if ((int)threadIdx.x < Bp)
+        for (int qq = 0; qq < Q; ++qq) tot += s_tmp[qq * Bp + threadIdx.x];
+    return tot;
+}
 
 // Grid-wide barrier: every CTA adds one arrival and waits until all G arrivals of this
 // barrier are in (the count is cumulative over the launch: barrier j completes at j G).
@@ -83,21 +109,48 @@ __device__ __forceinline__ bool grid_barrier(const PersistArgs& A, unsigned& epo
     return s_ok != 0;
 }
 
-// Per-slot total over the G partial rows part[g * 2 Bp + off + slot], in the same fixed
-// order in every CTA; returned in threads t < Bp.
-__device__ __forceinline__ double slot_total(const double* part, int G, int Bp, int off, double* s_tmp) {
-    const int Q = blockDim.x / Bp;
-    const int b = threadIdx.x % Bp, qd = threadIdx.x / Bp;
-    const int g0 = (int)((long long)G * qd / Q), g1 = (int)((long long)G * (qd + 1) / Q);
-    double s = 0.0;
-    for (int g = g0; g < g1; ++g) s += __ldcg(part + (long long)g * 2 * Bp + off + b);
+// Grid-wide barrier that also sums the partial rows: the last CTA to arrive (it sees the
+// arrival count reach the target) adds part[g][j Bp + b] over g in the fixed order of
+// slot_total into tot[j Bp + b] (j < nsum), then releases the others through bar[1]; the
+// others wait for the release and read the totals. One CTA reads the G partial rows instead
+// of every CTA. False if the wait ran out or another CTA gave up.
+__device__ __forceinline__ bool grid_barrier_sum(const PersistArgs& A, unsigned& epoch, int nsum, double* s_tmp) {
+    __shared__ int s_last, s_ok;
+    epoch += gridDim.x;
     __syncthreads();
-    s_tmp[threadIdx.x] = s;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned before = atomicAdd(A.bar, 1u);
+        s_last = before + 1u == epoch;
+        __threadfence();
+    }
     __syncthreads();
-    double tot = 0.0;
-    if ((int)threadIdx.x < Bp)
-        for (int qq = 0; qq < Q; ++qq) tot += s_tmp[qq * Bp + threadIdx.x];
-    return tot;
+    if (s_last) {
+        for (int j = 0; j < nsum; ++j) {
+            const double t = slot_total(A.part, gridDim.x, A.Bp, j * A.Bp, s_tmp);
+            if ((int)threadIdx.x < A.Bp) A.tot[j * A.Bp + threadIdx.x] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(A.bar + 1), "r"(epoch) : "memory");
+            s_ok = 1;
+        }
+    } else if (threadIdx.x == 0) {
+        int ok = 0;
+        for (unsigned t = 0; t < PERSIST_POLLS; ++t) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(A.bar + 1) : "memory");
+            if (v >= epoch) { ok = 1; break; }
+            if (*(volatile int*)A.err) break;
+            __nanosleep(64);
+        }
+        if (!ok) atomicCAS(A.err, 0, 3);
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // The CTA's per-slot sums (cta_lane_sum order) into its partial row, at offset `off`.
@@ -178,10 +231,10 @@ __global__ void __launch_bounds__(POD2G_THREADS, 2) k_persist(const PersistArgs 
             }
             put_partial(A, (double)dh + (double)dl, 0, s_tmp, s_out);
         }
-        if (!(ok = grid_barrier(A, epoch))) break;
+        if (!(ok = grid_barrier_sum(A, epoch, 1, s_tmp))) break;
         // ---- C: alpha, x += alpha p, r -= alpha q
         {
-            const double pq = slot_total(A.part, G, Bp, 0, s_tmp);
+            const double pq = tid < Bp ? __ldcg(A.tot + tid) : 0.0;
             if (tid < Bp) {
                 SlotScalars& S = s_sc[tid];
                 if (S.state == SLOT_ACTIVE) {
@@ -288,10 +341,10 @@ __global__ void __launch_bounds__(POD2G_THREADS, 2) k_persist(const PersistArgs 
                 }
             }
         }
-        if (!(ok = grid_barrier(A, epoch))) break;
+        if (!(ok = grid_barrier_sum(A, epoch, 1, s_tmp))) break;
         // ---- E: convergence test on ||r||^2, coarse solve for the slots b = blockIdx.x (mod G)
         {
-            const double rr = slot_total(A.part, G, Bp, 0, s_tmp);
+            const double rr = tid < Bp ? __ldcg(A.tot + tid) : 0.0;
             if (tid < Bp) {
                 SlotScalars& S = s_sc[tid];
                 if (S.state == SLOT_ACTIVE) {
@@ -314,7 +367,15 @@ __global__ void __launch_bounds__(POD2G_THREADS, 2) k_persist(const PersistArgs 
                     double cs = 0.0;
                     if (qd < Q) {
                         const int g0 = (int)((long long)G * qd / Q), g1 = (int)((long long)G * (qd + 1) / Q);
-                        for (int g = g0; g < g1; ++g) cs += __ldcg(A.cpart + ((long long)g * Bp + b) * kp + m);
+                        int g = g0;
+                        for (; g + 8 <= g1; g += 8) {   // eight loads in flight, added in order
+                            double v[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) v[j] = __ldcg(A.cpart + ((long long)(g + j) * Bp + b) * kp + m);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) cs += v[j];
+                        }
+                        for (; g < g1; ++g) cs += __ldcg(A.cpart + ((long long)g * Bp + b) * kp + m);
                     }
                     __syncthreads();
                     s_tmp[tid] = cs;
@@ -387,11 +448,11 @@ __global__ void __launch_bounds__(POD2G_THREADS, 2) k_persist(const PersistArgs 
             put_partial(A, (double)h + (double)l, 0, s_tmp, s_out);
             if (A.pr) put_partial(A, (double)xh + (double)xl, Bp, s_tmp, s_out);
         }
-        if (!(ok = grid_barrier(A, epoch))) break;
+        if (!(ok = grid_barrier_sum(A, epoch, A.pr ? 2 : 1, s_tmp))) break;
         // ---- beta
         {
-            const double rs = slot_total(A.part, G, Bp, 0, s_tmp);
-            const double rsx = A.pr ? slot_total(A.part, G, Bp, Bp, s_tmp) : 0.0;
+            const double rs = tid < Bp ? __ldcg(A.tot + tid) : 0.0;
+            const double rsx = A.pr && tid < Bp ? __ldcg(A.tot + Bp + tid) : 0.0;
             if (tid < Bp) {
                 SlotScalars& S = s_sc[tid];
                 if (S.state == SLOT_ACTIVE) {
@@ -474,11 +535,12 @@ int persist_launch(pod2g_ctx* c, int iters) {
     A.r1 = c->d_y32;
     A.ec = c->d_ec;
     A.part = c->d_part;
+    A.tot = c->d_part + (size_t)2 * c->Bp * 4 * c->num_sms;   // after the partial rows of 4 * SMs CTAs
     A.cpart = c->d_cpart;
     A.sc = c->d_sc;
     A.bar = c->d_counters + CNT_PERSIST;
     A.err = c->d_err;
-    P2G_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(unsigned), c->stream));
+    P2G_CUDA(cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), c->stream));
     void* args[] = {&A};
     P2G_CUDA(cudaLaunchCooperativeKernel(persist_fn(c->bs), dim3(c->grid_persist), dim3(POD2G_THREADS), args,
                                          persist_smem(c), c->stream));
