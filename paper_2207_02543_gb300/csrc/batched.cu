@@ -1090,22 +1090,24 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
 // ---------------------------------------------------------------------------- single-instance row kernels
 // For one slot lane (Bp = 1) a block row's values are one contiguous run ([block][bs*bs]); a
 // thread per row would walk it alone with strided, uncoalesced loads. Here a group of LPR lanes
-// (32 for 3 x 3 blocks, 16 otherwise) owns a row: lane t takes blocks beg + t, beg + t + LPR, ...,
-// so a group reads the row's values as one coalesced run and all its gathers are in flight at
-// once; the bs partial sums are then combined across the group by a fixed butterfly of shuffles
-// (double-float additions for the SpMV), and lane a < bs writes output a. KIND as k_rows_ws.
+// owns a row: lane t takes blocks beg + t, beg + t + LPR, ..., so a group reads the row's values
+// as coalesced runs and its gathers are in flight at once; the bs partial sums are then combined
+// across the group by a fixed butterfly of shuffles, and lane a < bs writes output a. The
+// smoothing passes (FP32 additions in the butterfly) use 32 lanes for 3 x 3 blocks and 16
+// otherwise; the SpMV, whose butterfly adds double-float pairs (~30 instructions a step), uses 8,
+// so that each lane multiplies several blocks per butterfly step. KIND as k_rows_ws.
 template <int BS, int KIND>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
 k_rows_v1(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
           const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ vin,
           const float* __restrict__ yin, float2* __restrict__ qout, float* __restrict__ out, double* part,
           unsigned* counter, SlotScalars* sc) {
-    constexpr int LPR = BS == 3 ? 32 : 16;
+    constexpr int LPR = KIND == 0 ? 8 : (BS == 3 ? 32 : 16);
     constexpr int BB = BS * BS;
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[2 * POD2G_MAX_BP];
     const int sub = threadIdx.x & (LPR - 1);
-    const unsigned gmask = LPR == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (threadIdx.x & (32 - LPR)));
     const bool on = sc[0].state == want;
     const float w = (float)D.omega;
     float d1h = 0.f, d1l = 0.f, d2h = 0.f, d2l = 0.f;
@@ -1116,6 +1118,7 @@ k_rows_v1(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
             float ah[BS], al[BS];
 #pragma unroll
             for (int a = 0; a < BS; ++a) { ah[a] = 0.f; al[a] = 0.f; }
+#pragma unroll 2
             for (int blk = beg + sub; blk < end; blk += LPR) {
                 const int j = __ldg(col_idx + blk);
                 float v[BB];
