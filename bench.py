@@ -677,9 +677,9 @@ def gb300_arm(args):
 
 def small_problem_entry(pkg, tol):
     """Q1 64 x 64 diffusion (3,969 unknowns, k = 10): the plain FP64 path on one query (host-checked
-    convergence every iteration), and the batched mixed path at batch 1 and 64, in its default form for a
-    problem this small (whole iterations in one persistent launch) and as a CUDA graph of 8 iterations
-    per launch: per-iteration times show the launch and latency cost of a problem this small."""
+    convergence every iteration), and the batched mixed path at batch 1 and 64, with whole iterations in
+    one persistent launch per 8 iterations and as a CUDA graph of 8 iterations per launch (the default):
+    per-iteration times show the launch and latency cost of a problem this small."""
     import torch
     from synth.problems import Workload
     from synth.snapshots import pod_basis
@@ -711,9 +711,11 @@ def small_problem_entry(pkg, tol):
         tune = s.get_tuning()
         if form == "graph":
             assert s.set_tuning(rows_kernel=tune["rows_kernel"] & 7) == pkg.OK
-        elif not tune["rows_kernel"] & 8:
+        elif tune["grid_persist"] < 1:   # the persistent form does not apply to this context
             s.close()
             continue
+        else:
+            assert s.set_tuning(rows_kernel=tune["rows_kernel"] | 8) == pkg.OK
         for _ in range(2):
             it, rel, sts, rc = s.solve_batch_dev(slots, b_dev, x_dev, tol=tol, maxit=MAXIT)
         torch.cuda.synchronize()

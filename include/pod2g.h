@@ -379,9 +379,10 @@ typedef struct {
                                post-smoothing as a sweep. Bit 3: whole iterations run in one
                                cooperative launch of grid_persist CTAs with grid-wide barriers between
                                the phases (assembled, Jacobi with r1 = r2 = 1, at most 64 slot lanes,
-                               K Phi stored or no coarse space); default where n * lanes <= 2^20, for
-                               which the eight launches per iteration of the graph path cost more than
-                               their work. Default: every other form the context supports. */
+                               K Phi stored or no coarse space; K Phi is kept for this where n * lanes
+                               <= 2^20); not a default (it measured at best at parity with the graph
+                               path), the autotuner selects it where it is faster. Default: every other
+                               form the context supports. */
     int32_t restrict_rows;  /* rows of Phi and r1 per shared-memory chunk of the bulk-staged
                                restriction (its tile; multiple of 4, 4..256, within 200 KB of shared
                                memory; 4 or more slot lanes); 0 = the default (~24 KB per chunk) */

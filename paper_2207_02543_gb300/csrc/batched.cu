@@ -1092,17 +1092,17 @@ k_post(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int3
 // thread per row would walk it alone with strided, uncoalesced loads. Here a group of LPR lanes
 // owns a row: lane t takes blocks beg + t, beg + t + LPR, ..., so a group reads the row's values
 // as coalesced runs and its gathers are in flight at once; the bs partial sums are then combined
-// across the group by a fixed butterfly of shuffles, and lane a < bs writes output a. The
-// smoothing passes (FP32 additions in the butterfly) use 32 lanes for 3 x 3 blocks and 16
-// otherwise; the SpMV, whose butterfly adds double-float pairs (~30 instructions a step), uses 8,
-// so that each lane multiplies several blocks per butterfly step. KIND as k_rows_ws.
+// across the group by a fixed butterfly of shuffles, and lane a < bs writes output a. LPR = 8:
+// each lane takes several blocks of a row between butterfly steps (the SpMV's steps add
+// double-float pairs, ~30 instructions each), measured faster than 32 lanes with a block each
+// for the SpMV and the smoothing passes. KIND as k_rows_ws.
 template <int BS, int KIND>
 __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(POD2G_THREADS)
 k_rows_v1(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
           const float* __restrict__ vals, const float* __restrict__ dinv, const float2* __restrict__ vin,
           const float* __restrict__ yin, float2* __restrict__ qout, float* __restrict__ out, double* part,
           unsigned* counter, SlotScalars* sc) {
-    constexpr int LPR = KIND == 0 ? 8 : (BS == 3 ? 32 : 16);
+    constexpr int LPR = 8;
     constexpr int BB = BS * BS;
     __shared__ double s_tmp[POD2G_THREADS];
     __shared__ double s_out[2 * POD2G_MAX_BP];
@@ -2087,18 +2087,19 @@ int batched_alloc(pod2g_ctx* c) {
     c->grid_vec = 8 * c->num_sms;
     c->rows_kernel = c->d_W32 ? 4 : 0;
     if (v1_applies(c)) {
-        // single instance: the group-per-row smoothing kernels by default (the per-thread SpMV was
-        // measured faster than the group-per-row one; the autotuner compares both forms)
+        // single instance: the group-per-row smoothing kernels by default, and the group-per-row SpMV
+        // for 3 x 3 blocks (measured faster than one thread per block row there, slower for 2 x 2
+        // blocks); the autotuner compares both forms
         int occ = 0;
         if (c->bs == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<1, 0>, POD2G_THREADS, 0);
         else if (c->bs == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<2, 0>, POD2G_THREADS, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_v1<3, 0>, POD2G_THREADS, 0);
         cudaGetLastError();
         if (occ > 0) {
-            c->rows_kernel |= 1;
+            c->rows_kernel |= c->bs == 3 ? 3 : 1;
             c->ws_occ = occ;
             // no more CTAs than rows to cover (a group of lanes per row, 256 / LPR rows per CTA)
-            const int lpr = c->bs == 3 ? 32 : 16;
+            const int lpr = 8;
             const int need = ceil_div(c->nb, POD2G_THREADS / lpr);
             c->grid_rows = std::max(CLUSTER, std::min(std::min(8 * c->num_sms, occ * c->num_sms),
                                                       ceil_div(need, CLUSTER) * CLUSTER) / CLUSTER * CLUSTER);
@@ -2129,13 +2130,12 @@ int batched_alloc(pod2g_ctx* c) {
             c->grid_spmv = c->grid_rows;
         }
     }
-    // whole iterations in one launch: as many CTAs as the rows need (256 row-slot items each),
-    // all resident at once; the default for problems small enough to be launch-bound
+    // whole iterations in one launch (rows_kernel bit 3): as many CTAs as the rows need (256
+    // row-slot items each), all resident at once. Not the default: on the problems measured it was
+    // at best at parity with the graph of kernels (a few thousand unknowns) and slower above that;
+    // the autotuner selects it where it measures faster
     const int pmax = std::min(persist_max_grid(c), 4 * c->num_sms);
-    if (pmax > 0) {
-        c->grid_persist = std::max(1, std::min(pmax, ceil_div((long long)c->nb * c->Bp, POD2G_THREADS)));
-        if ((long long)c->n * c->Bp <= POD2G_PERSIST_ITEMS) c->rows_kernel |= 8;
-    }
+    if (pmax > 0) c->grid_persist = std::max(1, std::min(pmax, ceil_div((long long)c->nb * c->Bp, POD2G_THREADS)));
     if (c->precision != POD2G_FP64 && c->kp > 0) {
         const int sm_r = (int)(restrict_bulk_smem(c) ? restrict_bulk_smem(c) : restrict_smem(c->Bp, c->kp));
         const int lb = restrict_lb(c->Bp, c->kp);

@@ -22,7 +22,7 @@
 #define POD2G_MAX_BP 256       // largest slot-lane count
 #define POD2G_ELEM_RE 8        // element positions per block row (elements adjacent to one node)
 #define POD2G_KREF_MAX 576     // reference-matrix entries, (npe * bs)^2 with npe * bs <= 24
-#define POD2G_PERSIST_ITEMS (1LL << 20)  // unknowns x slot lanes up to which whole iterations run in one launch by default
+#define POD2G_PERSIST_ITEMS (1LL << 20)  // unknowns x slot lanes up to which K Phi is kept for the persistent launch
 
 // ---------------------------------------------------------------------------- slot states
 enum SlotState : int { SLOT_IDLE = 0, SLOT_JOINING = 1, SLOT_ACTIVE = 2, SLOT_DONE = 3 };

@@ -1,10 +1,12 @@
-// Persistent PCG iterations for small problems: one cooperative launch runs up to
+// Persistent PCG iterations (an option for small problems): one cooperative launch runs up to
 // `iters` whole iterations of Algorithm 3 (PCG preconditioned by one two-grid cycle
 // AMG(0; K, r, r1, r2) of Algorithm 2 with P = Phi_r, Section 3.3; damped Jacobi,
 // r1 = r2 = 1) for the ACTIVE lanes of a batch. Where the matrix and vectors of all
 // slots are a few MB, the eight kernels per iteration of the graph path are bound by
 // their launch and drain latency, not by bytes; here the phases of an iteration are
-// separated by grid-wide barriers instead of kernel boundaries.
+// separated by grid-wide barriers instead of kernel boundaries. (Measured, it reaches
+// parity with the graph at a few thousand unknowns and loses above; the autotuner
+// decides.)
 //
 // Phases of one iteration (| = grid barrier):
 //   A  p = s + beta p                                                          |

@@ -1,6 +1,6 @@
 """The persistent form of the batched path: whole PCG iterations (Algorithm 3 with the
 two-grid preconditioner of Algorithm 2, Section 3.3) in one cooperative launch with
-grid-wide barriers between the phases, the default for small problems.
+grid-wide barriers between the phases (rows_kernel bit 3, selected explicitly here).
 
 It regroups partial sums only, so the bar is the same as for every launch shape:
 relative x error <= 1e-6 against the oracle at tol 1e-8, iteration counts within +-2,
@@ -60,9 +60,9 @@ def test_persistent_matches_oracle_and_graph(pkg, name, m):
     for form in ("persist", "persist", "graph"):
         s, vals = _solver(pkg, wl, Phi, m)
         t = s.get_tuning()
-        assert t["rows_kernel"] & PERSIST and t["grid_persist"] >= 1    # the default for a problem this small
-        if form == "graph":
-            assert s.set_tuning(rows_kernel=t["rows_kernel"] & 7) == pkg.OK
+        assert t["grid_persist"] >= 1 and not t["rows_kernel"] & PERSIST   # available, not the default
+        if form == "persist":
+            assert s.set_tuning(rows_kernel=t["rows_kernel"] | PERSIST) == pkg.OK
         X, it, rel, st, rc = s.solve_batch(list(range(m)), Bm, tol=TOL, maxit=3000)
         assert rc == pkg.OK and np.all(st == pkg.OK)
         assert np.all(rel <= TOL * 1.5)
@@ -127,7 +127,7 @@ def test_persistent_variants_match_oracle(pkg, variant):
     Bm = wl.rhs(m)
     kw = dict(beta_pr=True) if variant == "pr" else dict(method=pkg.STATIONARY)
     s, vals = _solver(pkg, wl, Phi, m, **kw)
-    assert s.get_tuning()["rows_kernel"] & PERSIST
+    assert s.set_tuning(rows_kernel=s.get_tuning()["rows_kernel"] | PERSIST) == pkg.OK
     X, it, rel, st, rc = s.solve_batch(list(range(m)), Bm, tol=TOL, maxit=5000)
     assert rc == pkg.OK and np.all(st == pkg.OK)
     s.close()
