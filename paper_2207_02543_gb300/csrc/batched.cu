@@ -1479,7 +1479,7 @@ k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
         }
     };
 
-    WsCur C{blockIdx.x * (POD2G_THREADS / 32) + warp, 0, 0, 0, 0};
+    WsCur C{(int)blockIdx.x * (POD2G_THREADS / 32) + warp, 0, 0, 0, 0};
     if (!work) C.g = NG;
     load_group(C);
     int t = 0, issued = 0;
@@ -1555,9 +1555,7 @@ k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
                         al[a][0] = lo.x; al[a][1] = lo.y;
                     }
                 }
-                continue;
-            }
-            if constexpr (KIND == 0 && SPT == 1 && BS >= 2) {
+            } else if constexpr (KIND == 0 && SPT == 1 && BS >= 2) {
                 // columns 0 and 1 of the block in packed instructions, into two accumulators per
                 // row (column 2 of a 3x3 block goes to the first, scalar); the two are added in
                 // double-float at the end of the row
@@ -1573,22 +1571,22 @@ k_rows_ws(Dims D, int want, int pr, const int32_t* __restrict__ row_ptr, const i
                     al[a][0] = lo.x; bl[a] = lo.y;
                     if constexpr (BS == 3) df_acc_fma(ah[a][0], al[a][0], va[2 * Bp], G[u][2][0].x, G[u][2][0].y);
                 }
-                continue;
-            }
+            } else {
 #pragma unroll
-            for (int a = 0; a < BS; ++a)
+                for (int a = 0; a < BS; ++a)
 #pragma unroll
-                for (int cc = 0; cc < BS; ++cc) {
-                    float v[SPT];
-                    ws_ld1<SPT>(vb + (u * BB + a * BS + cc) * Bp, v);
+                    for (int cc = 0; cc < BS; ++cc) {
+                        float v[SPT];
+                        ws_ld1<SPT>(vb + (u * BB + a * BS + cc) * Bp, v);
 #pragma unroll
-                    for (int s = 0; s < SPT; ++s) {
-                        if constexpr (KIND == 0) df_acc_fma(ah[a][s], al[a][s], v[s], G[u][cc][s].x, G[u][cc][s].y);
-                        else if constexpr (KIND == 1)
-                            ah[a][s] = __fmaf_rn(v[s], w * G[u][cc][s].y * G[u][cc][s].x, ah[a][s]);
-                        else ah[a][s] = __fmaf_rn(v[s], G[u][cc][s], ah[a][s]);
+                        for (int s = 0; s < SPT; ++s) {
+                            if constexpr (KIND == 0) df_acc_fma(ah[a][s], al[a][s], v[s], G[u][cc][s].x, G[u][cc][s].y);
+                            else if constexpr (KIND == 1)
+                                ah[a][s] = __fmaf_rn(v[s], w * G[u][cc][s].y * G[u][cc][s].x, ah[a][s]);
+                            else ah[a][s] = __fmaf_rn(v[s], G[u][cc][s], ah[a][s]);
+                        }
                     }
-                }
+            }
         }
         if (C.c == C.nch - 1) {
             const int i = C.g * RPW + r;
