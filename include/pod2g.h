@@ -371,7 +371,8 @@ typedef struct {
                                outer SpMV use the warp-staged kernels (each warp copies the matrix
                                values of its rows into shared memory with bulk asynchronous copies
                                ahead of use; assembled operators with 4..64 slot lanes and Jacobi
-                               relaxation); bit 2: the prolongation and post-smoothing run as one
+                               relaxation) or, with one slot lane, the kernels that give each block row
+                               a group of 8 lanes; bit 2: the prolongation and post-smoothing run as one
                                pass that forms K y2 = (r - r1) + (K Phi) e_c from K Phi stored per slot
                                at set-up, without a sweep over the matrix (contexts that store K Phi:
                                assembled, Jacobi with r1 = r2 = 1, K Phi smaller than the values and
@@ -381,8 +382,9 @@ typedef struct {
                                the phases (assembled, Jacobi with r1 = r2 = 1, at most 64 slot lanes,
                                K Phi stored or no coarse space; K Phi is kept for this where n * lanes
                                <= 2^20); not a default (it measured at best at parity with the graph
-                               path), the autotuner selects it where it is faster. Default: every other
-                               form the context supports. */
+                               path), the autotuner selects it where it is faster. Default: bits 0, 1
+                               and 2 where the context supports them, except bit 1 with one slot lane
+                               and 1x1 or 2x2 blocks (one thread per row measured faster there). */
     int32_t restrict_rows;  /* rows of Phi and r1 per shared-memory chunk of the bulk-staged
                                restriction (its tile; multiple of 4, 4..256, within 200 KB of shared
                                memory; 4 or more slot lanes); 0 = the default (~24 KB per chunk) */
