@@ -10,7 +10,8 @@
 * special cases: full coarse space => one iteration; b in K Phi with r1 = 0 =>
   one iteration and x = Phi c; empty coarse space => two damped-Jacobi sweeps
   B = 2S - S K S; Phi -> Phi Q invariance; x0 = x* => 0 iterations; f = 0;
-* planted mistakes: modified copies of oracle steps fail the pins above.
+* planted mistakes: modified copies of oracle steps fail the pins above;
+* the power-iteration estimate of rho(D^-1 K) vs the dense eigenvalues of D^-1/2 K D^-1/2.
 """
 import numpy as np
 import pytest
@@ -538,3 +539,16 @@ def test_rom_solution_is_the_galerkin_projection():
     assert np.allclose(x, Phi @ coef, rtol=1e-9, atol=1e-12 * np.abs(xs).max())
     c = np.random.default_rng(3).standard_normal(5)
     assert np.allclose(O.rom_solution(K, Phi, Kd @ (Phi @ c)), Phi @ c, rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- smoother bound
+@pytest.mark.parametrize("kind,ne", [("q4", 4), ("hex8", 3), ("q1", 6)])
+def test_spectral_radius_estimate_matches_dense_eigenvalues(kind, ne):
+    """rho(D^-1 K) from power iteration against the largest eigenvalue of the symmetric similar
+    matrix D^-1/2 K D^-1/2 (dense, LAPACK), which bounds the admissible Jacobi damping (omega rho < 2)."""
+    P, K = _small_system(3, ne=ne, kind=kind)
+    Dinv = O.jacobi_inverse_diagonal(K)
+    s = np.sqrt(Dinv)
+    lam = np.linalg.eigvalsh(s[:, None] * K.toarray() * s[None, :]).max()
+    est = O.spectral_radius_estimate(K, Dinv, 400)
+    assert abs(est - lam) <= 0.02 * lam, (est, lam)
